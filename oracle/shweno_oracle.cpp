@@ -1,0 +1,949 @@
+/*
+ * ADER-SHWENO oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded FP64 CPU restatement of the one-stage ADER scheme with the
+ * simple HWENO (SHWENO) reconstruction of Luo, Li, Qiu, Zhu and Chen, "A compact simple HWENO
+ * scheme with ADER time discretization for hyperbolic conservation laws I: structured meshes"
+ * (arXiv 2304.09724).  It exists so that the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark have something independent to compare the CUDA library against.  The library
+ * never links, loads or calls it, and it shares no code, header, table or generator with the
+ * library.
+ *
+ * Every step follows the paper's order (Section 4, Steps 1-5) and is written for a reader to
+ * check against the paper by eye, with no fusion, blocking or reordering:
+ *   Step 1  SHWENO reconstruction (Section 2.4 and Section 3.2).  The paper omits the 1D
+ *           procedure and defers to the simple HWENO of its reference [li2021]; this file takes
+ *           the following reading of it: one quartic on {I_{j-1}, I_j, I_{j+1}} that
+ *           matches the three cell averages and the two outer derivative averages, two linear
+ *           polynomials on {I_{j-1}, I_j} and {I_j, I_{j+1}}, linear weights (0.994, 0.003,
+ *           0.003), Jiang-Shu smoothness indicators and simple-WENO nonlinear weights.
+ *   Step 2  Lax-Wendroff / Cauchy-Kovalevskaya procedure (Eq. 2.6 and the 2D expressions of
+ *           Section 3.1), computed as the exact Taylor coefficients of a truncated power
+ *           series in (x, y, t) that satisfies W_t = -F(W)_x - G(W)_y term by term.
+ *   Step 3  Leading term from the exact (Burgers) or HLLC (Euler) Riemann solver, Eq. (2.5)
+ *           and (3.6); derivative terms from the linearised Riemann problems Eq. (2.8) and
+ *           (3.7) with the Jacobian at the leading term.
+ *   Step 4  State-expansion flux, Eq. (2.4), (2.9), (3.3)-(3.5), (3.8), with the 4-node
+ *           Gauss-Lobatto rule in time (Remark 2) and the 3-node Gauss rule along faces.
+ *   Step 5  Update of the cell averages, Eq. (2.2) and (3.2), and of the derivative averages
+ *           from the interface values at t_{n+1}, Eq. (2.11), (2.12), (3.10), (3.11).
+ * Pins for each function live in tests/test_oracle_*.py.
+ */
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+// ----------------------------------------------------------------------------------------
+// Problem description (the oracle's own; deliberately not the library's struct).
+// ----------------------------------------------------------------------------------------
+enum { EQ_BURGERS = 0, EQ_EULER = 1 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECTIVE = 2, BC_INFLOW = 3, BC_DMR_BOTTOM = 4,
+       BC_DMR_TOP = 5 };
+
+struct Problem {
+  int32_t dim, eq, nx, ny;
+  double x0, y0, dx, dy, gamma;
+  int32_t bc[4];         // x-low, x-high, y-low, y-high
+  double inflow[4][4];   // conserved state imposed by a BC_INFLOW side
+  int32_t linear;        // 1: every reconstruction uses the linear weights
+  double eps;            // epsilon in the nonlinear weights
+  double gam[3];         // linear weights gamma_1..3 (Section 2.4)
+};
+
+int ncomp(const Problem& P) {
+  if (P.eq == EQ_BURGERS) return 1;
+  return P.dim == 1 ? 3 : 4;
+}
+
+// ----------------------------------------------------------------------------------------
+// Quadrature rules.
+// ----------------------------------------------------------------------------------------
+// Gauss-Lobatto with 4 nodes on [0,1] for the time integral of the flux, Eq. (2.9) and
+// Remark 2 (the rule contains both t_n and t_{n+1}); exact for polynomials of degree 5.
+void lobatto4(double lam[4], double w[4]) {
+  lam[0] = 0.0;
+  lam[1] = 0.5 - std::sqrt(5.0) / 10.0;
+  lam[2] = 0.5 + std::sqrt(5.0) / 10.0;
+  lam[3] = 1.0;
+  w[0] = 1.0 / 12.0; w[1] = 5.0 / 12.0; w[2] = 5.0 / 12.0; w[3] = 1.0 / 12.0;
+}
+// Gauss-Legendre with 3 nodes on [-1/2, 1/2] for the face integrals, Eq. (3.3), (3.4), (3.10).
+void gauss3(double s[3], double w[3]) {
+  s[0] = -std::sqrt(15.0) / 10.0; s[1] = 0.0; s[2] = std::sqrt(15.0) / 10.0;
+  w[0] = 5.0 / 18.0; w[1] = 8.0 / 18.0; w[2] = 5.0 / 18.0;
+}
+
+// ----------------------------------------------------------------------------------------
+// Small dense linear algebra (Gaussian elimination with partial pivoting).
+// ----------------------------------------------------------------------------------------
+// Solves A x = b for an n x n row-major A (n <= 8).  A and b are copied.
+void solve(int n, const double* A_in, const double* b_in, double* x) {
+  double A[8][9];
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) A[i][j] = A_in[i * n + j];
+    A[i][n] = b_in[i];
+  }
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+    if (piv != col)
+      for (int j = 0; j <= n; ++j) std::swap(A[piv][j], A[col][j]);
+    for (int r = col + 1; r < n; ++r) {
+      double f = A[r][col] / A[col][col];
+      for (int j = col; j <= n; ++j) A[r][j] -= f * A[col][j];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = A[i][n];
+    for (int j = i + 1; j < n; ++j) s -= A[i][j] * x[j];
+    x[i] = s / A[i][i];
+  }
+}
+// Inverse of an n x n matrix by solving for the columns of the identity.
+void invert(int n, const double* A, double* Ainv) {
+  for (int c = 0; c < n; ++c) {
+    double e[8] = {0}, col[8];
+    e[c] = 1.0;
+    solve(n, A, e, col);
+    for (int r = 0; r < n; ++r) Ainv[r * n + c] = col[r];
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// Step 1: the SHWENO reconstruction in one dimension (Section 2.4), on the local coordinate
+// xi = (x - x_j)/h in [-1/2, 1/2].  Input for cell j: the cell averages Wb = (W_{j-1}, W_j,
+// W_{j+1}) and the derivative averages scaled by h, v = (h V_{j-1}, h V_{j+1}).  Polynomials are
+// held as monomial coefficients c[0..4] in xi.
+// ----------------------------------------------------------------------------------------
+double mono_avg(int k, double a, double b) {  // (1/(b-a)) * integral_a^b xi^k d xi, b - a = 1
+  return (std::pow(b, k + 1) - std::pow(a, k + 1)) / (k + 1);
+}
+
+// Quartic p1 on the big stencil: its averages over cells -1, 0, +1 equal Wb, and the averages
+// of its xi-derivative over cells -1 and +1 equal v (the reading of the omitted procedure).
+// The five conditions are written out as rows of a 5x5 matrix; its inverse is formed once by
+// Gaussian elimination and applied to (Wb, v).
+const double* big_poly_inverse() {
+  static double Minv[25];
+  static bool ready = false;
+  if (!ready) {
+    double A[25];
+    for (int l = -1; l <= 1; ++l)
+      for (int k = 0; k < 5; ++k) A[(l + 1) * 5 + k] = mono_avg(k, l - 0.5, l + 0.5);
+    const int outer[2] = {-1, 1};
+    for (int r = 0; r < 2; ++r) {
+      int l = outer[r];
+      // average of p' over cell l = p(l + 1/2) - p(l - 1/2)
+      for (int k = 0; k < 5; ++k) A[(3 + r) * 5 + k] = std::pow(l + 0.5, k) - std::pow(l - 0.5, k);
+    }
+    invert(5, A, Minv);
+    ready = true;
+  }
+  return Minv;
+}
+void big_poly(const double Wb[3], const double v[2], double c[5]) {
+  const double* Minv = big_poly_inverse();
+  const double rhs[5] = {Wb[0], Wb[1], Wb[2], v[0], v[1]};
+  for (int k = 0; k < 5; ++k) {
+    double s = 0.0;
+    for (int r = 0; r < 5; ++r) s += Minv[k * 5 + r] * rhs[r];
+    c[k] = s;
+  }
+}
+// Linear polynomials on the two small stencils, matching two cell averages each.
+void small_polys(const double Wb[3], double c2[5], double c3[5]) {
+  for (int k = 0; k < 5; ++k) c2[k] = c3[k] = 0.0;
+  c2[0] = Wb[1]; c2[1] = Wb[1] - Wb[0];   // {I_{j-1}, I_j}
+  c3[0] = Wb[1]; c3[1] = Wb[2] - Wb[1];   // {I_j, I_{j+1}}
+}
+// Jiang-Shu smoothness indicator beta = sum_{a>=1} integral_{-1/2}^{1/2} (d^a p / d xi^a)^2,
+// computed exactly by squaring the derivative polynomial and integrating its monomials.
+double smoothness(const double c[5]) {
+  double beta = 0.0;
+  double d[5];
+  for (int k = 0; k < 5; ++k) d[k] = c[k];
+  for (int a = 1; a <= 4; ++a) {
+    double nd[5] = {0};
+    for (int k = 1; k < 5; ++k) nd[k - 1] = k * d[k];
+    for (int k = 0; k < 5; ++k) d[k] = nd[k];
+    double sq[9] = {0};
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j) sq[i + j] += d[i] * d[j];
+    for (int k = 0; k < 9; k += 2) beta += sq[k] * 2.0 * std::ldexp(1.0, -(k + 1)) / (k + 1);
+  }
+  return beta;
+}
+// Nonlinear weights of the simple-WENO form: tau = ((|b1-b2| + |b1-b3|)/2)^2 and
+// w_l proportional to gamma_l (1 + tau/(beta_l + eps)).  linear=1 returns gamma itself.
+void shweno_weights(const double Wb[3], const double v[2], int linear, double eps,
+                    const double gam[3], double w[3]) {
+  if (linear) { for (int l = 0; l < 3; ++l) w[l] = gam[l]; return; }
+  double c1[5], c2[5], c3[5];
+  big_poly(Wb, v, c1);
+  small_polys(Wb, c2, c3);
+  double b[3] = {smoothness(c1), smoothness(c2), smoothness(c3)};
+  double tau = 0.5 * (std::fabs(b[0] - b[1]) + std::fabs(b[0] - b[2]));
+  tau = tau * tau;
+  double s = 0.0;
+  for (int l = 0; l < 3; ++l) { w[l] = gam[l] * (1.0 + tau / (b[l] + eps)); s += w[l]; }
+  for (int l = 0; l < 3; ++l) w[l] /= s;
+}
+// Combined SHWENO polynomial p = w1 (p1/g1 - g2/g1 p2 - g3/g1 p3) + w2 p2 + w3 p3 for given
+// weights.  With w = gamma it is p1.  The same weights serve the value and every derivative
+// (end of Section 2.1.2).
+void shweno_poly(const double Wb[3], const double v[2], const double w[3], const double gam[3],
+                 double c[5]) {
+  double c1[5], c2[5], c3[5];
+  big_poly(Wb, v, c1);
+  small_polys(Wb, c2, c3);
+  for (int k = 0; k < 5; ++k)
+    c[k] = w[0] * (c1[k] / gam[0] - gam[1] / gam[0] * c2[k] - gam[2] / gam[0] * c3[k]) +
+           w[1] * c2[k] + w[2] * c3[k];
+}
+// d^k p / d xi^k at xi, k = 0..4.
+void poly_derivs(const double c[5], double xi, double d[5]) {
+  for (int k = 0; k < 5; ++k) {
+    double s = 0.0, xp = 1.0;
+    for (int i = k; i < 5; ++i) {
+      double f = 1.0;
+      for (int q = 0; q < k; ++q) f *= (i - q);
+      s += c[i] * f * xp;
+      xp *= xi;
+    }
+    d[k] = s;
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// Physics (Eq. 2.1, 3.1, 5.1, 5.2): Burgers F = G = W^2/2; Euler with E = p/(g-1) + rho|u|^2/2.
+// ----------------------------------------------------------------------------------------
+void physical_flux(const Problem& P, int dir, const double* W, double* F) {
+  if (P.eq == EQ_BURGERS) { F[0] = 0.5 * W[0] * W[0]; return; }
+  const double g = P.gamma;
+  if (P.dim == 1) {
+    double rho = W[0], u = W[1] / rho, E = W[2];
+    double p = (g - 1.0) * (E - 0.5 * rho * u * u);
+    F[0] = rho * u; F[1] = rho * u * u + p; F[2] = u * (E + p);
+    return;
+  }
+  double rho = W[0], u = W[1] / rho, v = W[2] / rho, E = W[3];
+  double p = (g - 1.0) * (E - 0.5 * rho * (u * u + v * v));
+  double un = dir == 0 ? u : v;
+  F[0] = rho * un;
+  F[1] = W[1] * un + (dir == 0 ? p : 0.0);
+  F[2] = W[2] * un + (dir == 1 ? p : 0.0);
+  F[3] = un * (E + p);
+}
+
+// ----------------------------------------------------------------------------------------
+// Step 3a: leading term, the Godunov state at x/t = 0 of the conventional Riemann problem
+// Eq. (2.5) / (3.6).
+// ----------------------------------------------------------------------------------------
+// Exact solution of the Burgers Riemann problem sampled at x/t = 0.  A shock of speed
+// (uL+uR)/2 when uL > uR (speed 0 takes uL), otherwise a rarefaction fan (sonic point -> 0).
+double burgers_godunov(double uL, double uR) {
+  if (uL > uR) {
+    double s = 0.5 * (uL + uR);
+    return s >= 0.0 ? uL : uR;
+  }
+  if (uL >= 0.0) return uL;
+  if (uR <= 0.0) return uR;
+  return 0.0;
+}
+// HLLC state at x/t = 0 (Toro, "Riemann Solvers and Numerical Methods for Fluid Dynamics",
+// Section 10.4): Davis wave-speed estimates S_L = min(uL-cL, uR-cR), S_R = max(uL+cL, uR+cR),
+// contact speed S*, star states U*_K = rho_K (S_K-u_K)/(S_K-S*) (1, S*, v_K,
+// E_K/rho_K + (S*-u_K)(S* + p_K/(rho_K (S_K-u_K)))) with the normal and tangential velocity
+// placed by the face direction.  A wave of speed exactly 0 hands over its left-hand state.
+void hllc_state(const Problem& P, int dir, const double* WL, const double* WR, double* out) {
+  const double g = P.gamma;
+  const int nc = ncomp(P);
+  auto prim = [&](const double* W, double& rho, double& un, double& ut, double& p, double& c) {
+    rho = W[0];
+    if (nc == 3) { un = W[1] / rho; ut = 0.0; p = (g - 1.0) * (W[2] - 0.5 * rho * un * un); }
+    else {
+      double u = W[1] / rho, v = W[2] / rho;
+      un = dir == 0 ? u : v; ut = dir == 0 ? v : u;
+      p = (g - 1.0) * (W[3] - 0.5 * rho * (u * u + v * v));
+    }
+    c = std::sqrt(g * p / rho);
+  };
+  double rL, uL, tL, pL, cL, rR, uR, tR, pR, cR;
+  prim(WL, rL, uL, tL, pL, cL);
+  prim(WR, rR, uR, tR, pR, cR);
+  double SL = std::fmin(uL - cL, uR - cR);
+  double SR = std::fmax(uL + cL, uR + cR);
+  double Ss = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) /
+              (rL * (SL - uL) - rR * (SR - uR));
+  auto star = [&](const double* W, double r, double u, double t, double p, double S, double* U) {
+    double f = r * (S - u) / (S - Ss);
+    double Ek = W[nc - 1];
+    double e = Ek / r + (Ss - u) * (Ss + p / (r * (S - u)));
+    U[0] = f;
+    if (nc == 3) { U[1] = f * Ss; U[2] = f * e; }
+    else {
+      U[1 + dir] = f * Ss;
+      U[2 - dir] = f * t;
+      U[3] = f * e;
+    }
+  };
+  if (0.0 <= SL) { for (int q = 0; q < nc; ++q) out[q] = WL[q]; }
+  else if (0.0 <= Ss) star(WL, rL, uL, tL, pL, SL, out);
+  else if (0.0 <= SR) star(WR, rR, uR, tR, pR, SR, out);
+  else { for (int q = 0; q < nc; ++q) out[q] = WR[q]; }
+}
+
+// ----------------------------------------------------------------------------------------
+// Step 3b: linearised Riemann problems for the derivatives, Eq. (2.8) / (3.7).  With
+// A = F'(W*) = R diag(lambda) L the solution at x/t = 0 is R (H o L d_L + (1-H) o L d_R) where
+// H = 1 for lambda > 0, 0 for lambda < 0 and 1/2 for lambda = 0 (the average of both sides).
+// Right eigenvectors of the Euler Jacobian (Toro, Section 3.2), L = R^{-1} by elimination.
+// ----------------------------------------------------------------------------------------
+void eigensystem(const Problem& P, int dir, const double* W, double* lam, double* R) {
+  const int nc = ncomp(P);
+  if (P.eq == EQ_BURGERS) { lam[0] = W[0]; R[0] = 1.0; return; }
+  const double g = P.gamma;
+  if (nc == 3) {
+    double rho = W[0], u = W[1] / rho, E = W[2];
+    double p = (g - 1.0) * (E - 0.5 * rho * u * u);
+    double c = std::sqrt(g * p / rho), H = (E + p) / rho;
+    double r[3][3] = {{1.0, u - c, H - u * c}, {1.0, u, 0.5 * u * u}, {1.0, u + c, H + u * c}};
+    lam[0] = u - c; lam[1] = u; lam[2] = u + c;
+    for (int k = 0; k < 3; ++k)
+      for (int q = 0; q < 3; ++q) R[q * 3 + k] = r[k][q];
+    return;
+  }
+  double rho = W[0], u = W[1] / rho, v = W[2] / rho, E = W[3];
+  double p = (g - 1.0) * (E - 0.5 * rho * (u * u + v * v));
+  double c = std::sqrt(g * p / rho), H = (E + p) / rho;
+  double un = dir == 0 ? u : v;
+  double r[4][4];
+  if (dir == 0) {
+    double rr[4][4] = {{1.0, u - c, v, H - u * c}, {1.0, u, v, 0.5 * (u * u + v * v)},
+                       {0.0, 0.0, 1.0, v}, {1.0, u + c, v, H + u * c}};
+    std::memcpy(r, rr, sizeof(r));
+  } else {
+    double rr[4][4] = {{1.0, u, v - c, H - v * c}, {1.0, u, v, 0.5 * (u * u + v * v)},
+                       {0.0, 1.0, 0.0, u}, {1.0, u, v + c, H + v * c}};
+    std::memcpy(r, rr, sizeof(r));
+  }
+  lam[0] = un - c; lam[1] = un; lam[2] = un; lam[3] = un + c;
+  for (int k = 0; k < 4; ++k)
+    for (int q = 0; q < 4; ++q) R[q * 4 + k] = r[k][q];
+}
+
+void upwind(int nc, const double* lam, const double* R, const double* L, const double* dL,
+            const double* dR, double* out) {
+  double a[4];
+  for (int k = 0; k < nc; ++k) {
+    double aL = 0.0, aR = 0.0;
+    for (int q = 0; q < nc; ++q) { aL += L[k * nc + q] * dL[q]; aR += L[k * nc + q] * dR[q]; }
+    double H = lam[k] > 0.0 ? 1.0 : (lam[k] < 0.0 ? 0.0 : 0.5);
+    a[k] = H * aL + (1.0 - H) * aR;
+  }
+  for (int q = 0; q < nc; ++q) {
+    double s = 0.0;
+    for (int k = 0; k < nc; ++k) s += R[q * nc + k] * a[k];
+    out[q] = s;
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// Step 2: the Cauchy-Kovalevskaya procedure by truncated power series.
+// A series s holds the normalised Taylor coefficients s[m][n][k] = d^{m+n+k} f / (dx^m dy^n
+// dt^k) / (m! n! k!) at the interface point, for m + n + k <= 4.  Products and quotients of
+// series are the Cauchy products of the coefficient arrays.  The PDE W_t = -F_x - G_y says
+// (k+1) a[m][n][k+1] = -(m+1) f[m+1][n][k] - (n+1) g[m][n+1][k]; the time slices are filled one
+// after another, each from fluxes evaluated on the slices already known.  This gives the full
+// nonlinear expressions of Eq. (2.6) and of Section 3.1 ("and so on") to fourth order.
+// ----------------------------------------------------------------------------------------
+const int ORD = 4;
+struct Ser { double c[5][5][5]; };
+
+void ser_zero(Ser& s) { std::memset(s.c, 0, sizeof(s.c)); }
+bool in_range(int m, int n, int k) { return m + n + k <= ORD; }
+
+Ser ser_mul(const Ser& a, const Ser& b) {
+  Ser r; ser_zero(r);
+  for (int m = 0; m <= ORD; ++m)
+    for (int n = 0; m + n <= ORD; ++n)
+      for (int k = 0; m + n + k <= ORD; ++k) {
+        double s = 0.0;
+        for (int p = 0; p <= m; ++p)
+          for (int q = 0; q <= n; ++q)
+            for (int t = 0; t <= k; ++t) s += a.c[p][q][t] * b.c[m - p][n - q][k - t];
+        r.c[m][n][k] = s;
+      }
+  return r;
+}
+// q = a / b, from b * q = a solved index by index in lexicographic order (every index below a
+// given one in the product order comes first).
+Ser ser_div(const Ser& a, const Ser& b) {
+  Ser q; ser_zero(q);
+  for (int m = 0; m <= ORD; ++m)
+    for (int n = 0; m + n <= ORD; ++n)
+      for (int k = 0; m + n + k <= ORD; ++k) {
+        double s = a.c[m][n][k];
+        for (int p = 0; p <= m; ++p)
+          for (int r = 0; r <= n; ++r)
+            for (int t = 0; t <= k; ++t) {
+              if (p == m && r == n && t == k) continue;
+              s -= b.c[m - p][n - r][k - t] * q.c[p][r][t];
+            }
+        q.c[m][n][k] = s / b.c[0][0][0];
+      }
+  return q;
+}
+Ser ser_lin(double a, const Ser& x, double b, const Ser& y) {
+  Ser r; ser_zero(r);
+  for (int m = 0; m <= ORD; ++m)
+    for (int n = 0; n <= ORD; ++n)
+      for (int k = 0; k <= ORD; ++k) r.c[m][n][k] = a * x.c[m][n][k] + b * y.c[m][n][k];
+  return r;
+}
+
+// Flux series F (x-direction) and G (y-direction) of the state series W.
+void flux_series(const Problem& P, const Ser* W, Ser* F, Ser* G) {
+  const int nc = ncomp(P);
+  const double g = P.gamma;
+  if (P.eq == EQ_BURGERS) {
+    Ser h = ser_mul(W[0], W[0]);
+    F[0] = ser_lin(0.5, h, 0.0, h);
+    if (P.dim == 2) G[0] = F[0]; else ser_zero(G[0]);
+    return;
+  }
+  if (nc == 3) {
+    Ser u = ser_div(W[1], W[0]);
+    Ser mu = ser_mul(W[1], u);
+    Ser p = ser_lin(g - 1.0, W[2], -0.5 * (g - 1.0), mu);
+    Ser H = ser_lin(1.0, W[2], 1.0, p);
+    F[0] = W[1];
+    F[1] = ser_lin(1.0, mu, 1.0, p);
+    F[2] = ser_mul(u, H);
+    for (int q = 0; q < 3; ++q) ser_zero(G[q]);
+    return;
+  }
+  Ser u = ser_div(W[1], W[0]);
+  Ser v = ser_div(W[2], W[0]);
+  Ser mu = ser_mul(W[1], u);
+  Ser mv = ser_mul(W[1], v);
+  Ser nv = ser_mul(W[2], v);
+  Ser ke = ser_lin(0.5, mu, 0.5, nv);
+  Ser p = ser_lin(g - 1.0, W[3], -(g - 1.0), ke);
+  Ser H = ser_lin(1.0, W[3], 1.0, p);
+  F[0] = W[1];
+  F[1] = ser_lin(1.0, mu, 1.0, p);
+  F[2] = mv;
+  F[3] = ser_mul(u, H);
+  G[0] = W[2];
+  G[1] = mv;
+  G[2] = ser_lin(1.0, nv, 1.0, p);
+  G[3] = ser_mul(v, H);
+}
+
+// Fills the time slices k = 1..4 of W from its spatial slice k = 0.
+void cauchy_kovalevskaya(const Problem& P, Ser* W) {
+  const int nc = ncomp(P);
+  for (int k = 0; k < ORD; ++k) {
+    Ser F[4], G[4];
+    flux_series(P, W, F, G);
+    for (int q = 0; q < nc; ++q)
+      for (int m = 0; m <= ORD; ++m)
+        for (int n = 0; m + n + k + 1 <= ORD; ++n)
+          W[q].c[m][n][k + 1] =
+              -((m + 1) * F[q].c[m + 1][n][k] + (n + 1) * G[q].c[m][n + 1][k]) / (k + 1);
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// Steps 3-4 at one interface quadrature point: given the one-sided spatial derivatives
+// dL[q][m][n], dR[q][m][n] = d^{m+n} W_q / dx^m dy^n (m+n <= 4; in 1D n = 0), direction dir of
+// the face normal, returns the time-Taylor coefficients tc[q][k] = d^k W*/dt^k / k!.
+// ----------------------------------------------------------------------------------------
+typedef double Deriv[5][5];  // [m][n]
+
+double factorial(int k) { double f = 1.0; for (int i = 2; i <= k; ++i) f *= i; return f; }
+
+void grp_point(const Problem& P, int dir, const Deriv* dL, const Deriv* dR, double tc[4][5]) {
+  const int nc = ncomp(P);
+  double WL[4], WR[4], Ws[4];
+  for (int q = 0; q < nc; ++q) { WL[q] = dL[q][0][0]; WR[q] = dR[q][0][0]; }
+  if (P.eq == EQ_BURGERS) Ws[0] = burgers_godunov(WL[0], WR[0]);
+  else hllc_state(P, dir, WL, WR, Ws);
+  double lam[4], R[16], L[16];
+  eigensystem(P, dir, Ws, lam, R);
+  invert(nc, R, L);
+  Ser S[4];
+  for (int q = 0; q < nc; ++q) { ser_zero(S[q]); S[q].c[0][0][0] = Ws[q]; }
+  const int nmax = P.dim == 2 ? ORD : 0;
+  for (int m = 0; m <= ORD; ++m)
+    for (int n = 0; n <= nmax && m + n <= ORD; ++n) {
+      if (m == 0 && n == 0) continue;
+      double a[4], b[4], o[4];
+      for (int q = 0; q < nc; ++q) { a[q] = dL[q][m][n]; b[q] = dR[q][m][n]; }
+      upwind(nc, lam, R, L, a, b, o);
+      for (int q = 0; q < nc; ++q) S[q].c[m][n][0] = o[q] / (factorial(m) * factorial(n));
+    }
+  cauchy_kovalevskaya(P, S);
+  for (int q = 0; q < nc; ++q)
+    for (int k = 0; k <= ORD; ++k) tc[q][k] = S[q].c[0][0][k];
+}
+
+// State of the Taylor expansion Eq. (2.4) at tau.
+void taylor_state(int nc, const double tc[4][5], double tau, double* W) {
+  for (int q = 0; q < nc; ++q) {
+    double s = 0.0, tp = 1.0;
+    for (int k = 0; k <= ORD; ++k) { s += tc[q][k] * tp; tp *= tau; }
+    W[q] = s;
+  }
+}
+// Time-averaged flux of Eq. (2.9) with the Lobatto rule, and the state at tau = dt used by
+// Eq. (2.11) / (3.10) (Remark 1).
+void ader_flux(const Problem& P, int dir, const double tc[4][5], double dt, double* Fhat,
+               double* Wend) {
+  const int nc = ncomp(P);
+  double lam[4], w[4];
+  lobatto4(lam, w);
+  for (int q = 0; q < nc; ++q) Fhat[q] = 0.0;
+  for (int a = 0; a < 4; ++a) {
+    double W[4], F[4];
+    taylor_state(nc, tc, lam[a] * dt, W);
+    physical_flux(P, dir, W, F);
+    for (int q = 0; q < nc; ++q) Fhat[q] += w[a] * F[q];
+  }
+  taylor_state(nc, tc, dt, Wend);
+}
+
+// ----------------------------------------------------------------------------------------
+// Boundary conditions through ghost-cell lookup (Section 5 examples): periodic, outflow
+// (zero-order extrapolation of every cell quantity), reflective walls (mirror images with the
+// normal momentum and every derivative normal to the wall changing sign as the parity of the
+// mirrored field requires), an imposed inflow state, and the two double-Mach-reflection sides
+// of Example 5.10 (bottom: exact post-shock state for x < 1/6, reflective wall beyond; top:
+// exact Mach 10 shock at x = 1/6 + (y + 20 t)/sqrt(3), sampled at the ghost-cell centre).
+// Fields: 0 = W (averages), 1 = V (x-derivative averages), 2 = Y (y-derivative), 3 = Z (xy).
+// ----------------------------------------------------------------------------------------
+const double DMR_POST[4] = {8.0, 57.1597, -33.0012, 563.544};
+const double DMR_PRE[4] = {1.4, 0.0, 0.0, 2.5};
+
+struct State {
+  const Problem* P;
+  const double* f[4];  // W, V, Y, Z arrays [comp][ny][nx] (1D: ny = 1)
+  const uint8_t* flag; // per-cell troubled flag, or null (all nonlinear)
+  double t;
+};
+
+// Parity of field f, component q under the mirror normal to axis (0 = x, 1 = y).
+double mirror_sign(const Problem& P, int f, int q, int axis) {
+  double s = 1.0;
+  int normal_momentum = (P.eq == EQ_EULER) ? 1 + axis : -1;
+  if (q == normal_momentum) s = -s;
+  bool has_dx = (f == 1 || f == 3), has_dy = (f == 2 || f == 3);
+  if ((axis == 0 && has_dx) || (axis == 1 && has_dy)) s = -s;
+  return s;
+}
+
+double fetch(const State& S, int f, int q, int i, int j) {
+  const Problem& P = *S.P;
+  const int i0 = i, j0 = j;
+  double sign = 1.0;
+  if (i < 0 || i >= P.nx) {
+    int kind = i < 0 ? P.bc[0] : P.bc[1];
+    int side = i < 0 ? 0 : 1;
+    switch (kind) {
+      case BC_PERIODIC: i = ((i % P.nx) + P.nx) % P.nx; break;
+      case BC_OUTFLOW: i = i < 0 ? 0 : P.nx - 1; break;
+      case BC_REFLECTIVE: i = i < 0 ? -1 - i : 2 * P.nx - 1 - i; sign *= mirror_sign(P, f, q, 0); break;
+      default: return f == 0 ? P.inflow[side][q] : 0.0;  // imposed state, zero derivatives
+    }
+  }
+  if (P.dim == 2 && (j < 0 || j >= P.ny)) {
+    int kind = j < 0 ? P.bc[2] : P.bc[3];
+    int side = j < 0 ? 2 : 3;
+    double xc = P.x0 + (i0 + 0.5) * P.dx, yc = P.y0 + (j0 + 0.5) * P.dy;
+    if (kind == BC_DMR_BOTTOM) {
+      if (xc < 1.0 / 6.0) return f == 0 ? DMR_POST[q] : 0.0;
+      kind = BC_REFLECTIVE;
+    }
+    if (kind == BC_DMR_TOP) {
+      bool post = yc >= std::sqrt(3.0) * (xc - 1.0 / 6.0) - 20.0 * S.t;
+      return f == 0 ? (post ? DMR_POST[q] : DMR_PRE[q]) : 0.0;
+    }
+    switch (kind) {
+      case BC_PERIODIC: j = ((j % P.ny) + P.ny) % P.ny; break;
+      case BC_OUTFLOW: j = j < 0 ? 0 : P.ny - 1; break;
+      case BC_REFLECTIVE: j = j < 0 ? -1 - j : 2 * P.ny - 1 - j; sign *= mirror_sign(P, f, q, 1); break;
+      default: return f == 0 ? P.inflow[side][q] : 0.0;
+    }
+  }
+  return sign * S.f[f][((size_t)q * P.ny + j) * P.nx + i];
+}
+// Flag of the cell a reconstruction is anchored on; ghost cells take the flag of the interior
+// cell they copy, imposed-state ghosts count as troubled.
+int cell_flag(const State& S, int i, int j) {
+  if (!S.flag) return 1;
+  const Problem& P = *S.P;
+  if (i < 0 || i >= P.nx) {
+    int kind = i < 0 ? P.bc[0] : P.bc[1];
+    if (kind == BC_PERIODIC) i = ((i % P.nx) + P.nx) % P.nx;
+    else if (kind == BC_OUTFLOW) i = i < 0 ? 0 : P.nx - 1;
+    else if (kind == BC_REFLECTIVE) i = i < 0 ? -1 - i : 2 * P.nx - 1 - i;
+    else return 1;
+  }
+  if (P.dim == 2 && (j < 0 || j >= P.ny)) {
+    int kind = j < 0 ? P.bc[2] : P.bc[3];
+    if (kind == BC_PERIODIC) j = ((j % P.ny) + P.ny) % P.ny;
+    else if (kind == BC_OUTFLOW) j = j < 0 ? 0 : P.ny - 1;
+    else if (kind == BC_REFLECTIVE) j = j < 0 ? -1 - j : 2 * P.ny - 1 - j;
+    else return 1;
+  }
+  return S.flag[(size_t)j * P.nx + i] ? 1 : 0;
+}
+
+// One 1D SHWENO reconstruction evaluated at xi: derivatives d^k/dxi^k, k = 0..4.
+void recon_eval(const Problem& P, const double Wb[3], const double v[2], int nonlinear,
+                double xi, double d[5]) {
+  double w[3], c[5];
+  shweno_weights(Wb, v, P.linear || !nonlinear, P.eps, P.gam, w);
+  shweno_poly(Wb, v, w, P.gam, c);
+  poly_derivs(c, xi, d);
+}
+
+// ----------------------------------------------------------------------------------------
+// One time step in 1D (Section 2; Section 4 Steps 1-5).
+// ----------------------------------------------------------------------------------------
+void step1d(const Problem& P, const State& S, double dt, double* Wn, double* Vn) {
+  const int nc = ncomp(P), N = P.nx;
+  const double h = P.dx;
+  std::vector<double> Fh((size_t)(N + 1) * nc), We((size_t)(N + 1) * nc);
+  for (int fc = 0; fc <= N; ++fc) {  // face between cells fc-1 and fc
+    Deriv dL[4], dR[4];
+    std::memset(dL, 0, sizeof(dL)); std::memset(dR, 0, sizeof(dR));
+    for (int q = 0; q < nc; ++q) {
+      for (int side = 0; side < 2; ++side) {
+        int cell = fc - 1 + side;
+        double Wb[3] = {fetch(S, 0, q, cell - 1, 0), fetch(S, 0, q, cell, 0), fetch(S, 0, q, cell + 1, 0)};
+        double v[2] = {h * fetch(S, 1, q, cell - 1, 0), h * fetch(S, 1, q, cell + 1, 0)};
+        double d[5];
+        recon_eval(P, Wb, v, cell_flag(S, cell, 0), side == 0 ? 0.5 : -0.5, d);
+        for (int m = 0; m <= ORD; ++m) (side == 0 ? dL : dR)[q][m][0] = d[m] / std::pow(h, m);
+      }
+    }
+    double tc[4][5], F[4], Wend[4];
+    grp_point(P, 0, dL, dR, tc);
+    ader_flux(P, 0, tc, dt, F, Wend);
+    for (int q = 0; q < nc; ++q) { Fh[(size_t)fc * nc + q] = F[q]; We[(size_t)fc * nc + q] = Wend[q]; }
+  }
+  for (int j = 0; j < N; ++j)
+    for (int q = 0; q < nc; ++q) {
+      size_t o = (size_t)q * N + j;
+      Wn[o] = S.f[0][o] - dt / h * (Fh[(size_t)(j + 1) * nc + q] - Fh[(size_t)j * nc + q]);
+      Vn[o] = (We[(size_t)(j + 1) * nc + q] - We[(size_t)j * nc + q]) / h;
+    }
+}
+
+// ----------------------------------------------------------------------------------------
+// One time step in 2D (Section 3; Section 4 Steps 1-5), dimension by dimension (Section 3.2).
+// ----------------------------------------------------------------------------------------
+// y-direction reconstruction in column i, row j at eta: out[set][q][n] = d^n/dy^n of the line
+// average in x of W (set 0, from {W, Y}) or of W_x (set 1, from {V, Z}) at y = y_j + eta dy.
+void ypass(const State& S, int i, int j, double eta, double out[2][4][5]) {
+  const Problem& P = *S.P;
+  const int nc = ncomp(P);
+  for (int set = 0; set < 2; ++set)
+    for (int q = 0; q < nc; ++q) {
+      int fa = set == 0 ? 0 : 1, fd = set == 0 ? 2 : 3;
+      double Wb[3] = {fetch(S, fa, q, i, j - 1), fetch(S, fa, q, i, j), fetch(S, fa, q, i, j + 1)};
+      double v[2] = {P.dy * fetch(S, fd, q, i, j - 1), P.dy * fetch(S, fd, q, i, j + 1)};
+      double d[5];
+      recon_eval(P, Wb, v, cell_flag(S, i, j), eta, d);
+      for (int n = 0; n <= ORD; ++n) out[set][q][n] = d[n] / std::pow(P.dy, n);
+    }
+}
+// x-direction counterpart: out[set][q][m] = d^m/dx^m of the line average in y of W (set 0,
+// from {W, V}) or of W_y (set 1, from {Y, Z}) at x = x_i + xi dx.
+void xpass(const State& S, int i, int j, double xi, double out[2][4][5]) {
+  const Problem& P = *S.P;
+  const int nc = ncomp(P);
+  for (int set = 0; set < 2; ++set)
+    for (int q = 0; q < nc; ++q) {
+      int fa = set == 0 ? 0 : 2, fd = set == 0 ? 1 : 3;
+      double Wb[3] = {fetch(S, fa, q, i - 1, j), fetch(S, fa, q, i, j), fetch(S, fa, q, i + 1, j)};
+      double v[2] = {P.dx * fetch(S, fd, q, i - 1, j), P.dx * fetch(S, fd, q, i + 1, j)};
+      double d[5];
+      recon_eval(P, Wb, v, cell_flag(S, i, j), xi, d);
+      for (int m = 0; m <= ORD; ++m) out[set][q][m] = d[m] / std::pow(P.dx, m);
+    }
+}
+// Second pass across the face.  line[c][set][q][k] holds the first-pass output of the four
+// cells c = 0..3 of the stencil (cells a-1, a, a+1, a+2 along the normal; face between a and
+// a+1); k is the derivative order along the face.  The weights of each side come from the
+// k = 0 data and serve every k (reading of Section 3.2 with the remark ending Section 2.1.2).
+// Returns d[q][p][k]: p-th normal derivative of the k-th tangential derivative.
+void second_pass(const Problem& P, double hn, const double line[4][2][4][5], int flagL, int flagR,
+                 Deriv* dL, Deriv* dR) {
+  const int nc = ncomp(P);
+  for (int side = 0; side < 2; ++side) {
+    int base = side;  // stencil cells base..base+2; the reconstructed cell is base+1
+    double xi = side == 0 ? 0.5 : -0.5;
+    int fl = side == 0 ? flagL : flagR;
+    for (int q = 0; q < nc; ++q) {
+      double w[3];
+      {
+        double Wb[3] = {line[base][0][q][0], line[base + 1][0][q][0], line[base + 2][0][q][0]};
+        double v[2] = {hn * line[base][1][q][0], hn * line[base + 2][1][q][0]};
+        shweno_weights(Wb, v, P.linear || !fl, P.eps, P.gam, w);
+      }
+      for (int k = 0; k <= ORD; ++k) {
+        double Wb[3] = {line[base][0][q][k], line[base + 1][0][q][k], line[base + 2][0][q][k]};
+        double v[2] = {hn * line[base][1][q][k], hn * line[base + 2][1][q][k]};
+        double c[5], d[5];
+        shweno_poly(Wb, v, w, P.gam, c);
+        poly_derivs(c, xi, d);
+        for (int p = 0; p + k <= ORD; ++p) (side == 0 ? dL : dR)[q][p][k] = d[p] / std::pow(hn, p);
+      }
+    }
+  }
+}
+// Swaps the roles of the indices of a derivative table so that [m][n] is always
+// (x-order, y-order).
+void to_xy(int nc, const Deriv* in, int normal_is_x, Deriv* out) {
+  for (int q = 0; q < nc; ++q)
+    for (int a = 0; a <= ORD; ++a)
+      for (int b = 0; a + b <= ORD; ++b) {
+        if (normal_is_x) out[q][a][b] = in[q][a][b];
+        else out[q][b][a] = in[q][a][b];
+      }
+}
+
+void step2d(const Problem& P, const State& S, double dt, double* Wn, double* Vn, double* Yn,
+            double* Zn) {
+  const int nc = ncomp(P), nx = P.nx, ny = P.ny;
+  double gs[3], gw[3];
+  gauss3(gs, gw);
+  // x-faces (i+1/2, j), i = -1..nx-1: F-hat and the Gauss-weighted state at t_{n+1}.
+  std::vector<double> FX((size_t)(nx + 1) * ny * nc), WX((size_t)(nx + 1) * ny * nc);
+  std::vector<double> GY((size_t)nx * (ny + 1) * nc), WY((size_t)nx * (ny + 1) * nc);
+  std::vector<double> WC((size_t)(nx + 1) * (ny + 1) * nc);
+  for (int j = 0; j < ny; ++j)
+    for (int i = -1; i < nx; ++i) {
+      double Fs[4] = {0}, Ws[4] = {0};
+      for (int g = 0; g < 3; ++g) {
+        double line[4][2][4][5];
+        for (int c = 0; c < 4; ++c) ypass(S, i - 1 + c, j, gs[g], line[c]);
+        Deriv a[4], b[4], dL[4], dR[4];
+        second_pass(P, P.dx, line, cell_flag(S, i, j), cell_flag(S, i + 1, j), a, b);
+        to_xy(nc, a, 1, dL); to_xy(nc, b, 1, dR);
+        double tc[4][5], F[4], We[4];
+        grp_point(P, 0, dL, dR, tc);
+        ader_flux(P, 0, tc, dt, F, We);
+        for (int q = 0; q < nc; ++q) { Fs[q] += gw[g] * F[q]; Ws[q] += gw[g] * We[q]; }
+      }
+      for (int q = 0; q < nc; ++q) {
+        size_t o = ((size_t)j * (nx + 1) + (i + 1)) * nc + q;
+        FX[o] = Fs[q]; WX[o] = Ws[q];
+      }
+    }
+  // y-faces (i, j+1/2), j = -1..ny-1.
+  for (int j = -1; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      double Gs[4] = {0}, Ws[4] = {0};
+      for (int g = 0; g < 3; ++g) {
+        double line[4][2][4][5];
+        for (int c = 0; c < 4; ++c) xpass(S, i, j - 1 + c, gs[g], line[c]);
+        Deriv a[4], b[4], dB[4], dT[4];
+        second_pass(P, P.dy, line, cell_flag(S, i, j), cell_flag(S, i, j + 1), a, b);
+        to_xy(nc, a, 0, dB); to_xy(nc, b, 0, dT);
+        double tc[4][5], G[4], We[4];
+        grp_point(P, 1, dB, dT, tc);
+        ader_flux(P, 1, tc, dt, G, We);
+        for (int q = 0; q < nc; ++q) { Gs[q] += gw[g] * G[q]; Ws[q] += gw[g] * We[q]; }
+      }
+      for (int q = 0; q < nc; ++q) {
+        size_t o = ((size_t)(j + 1) * nx + i) * nc + q;
+        GY[o] = Gs[q]; WY[o] = Ws[q];
+      }
+    }
+  // Corners (i+1/2, j+1/2): the y-direction traces of rows j (eta = +1/2) and j+1 (eta = -1/2)
+  // are averaged, then one x-direction generalised Riemann problem is solved and evaluated at
+  // tau = dt ("in a similar way", Section 3.3).
+  for (int j = -1; j < ny; ++j)
+    for (int i = -1; i < nx; ++i) {
+      double line[4][2][4][5];
+      for (int c = 0; c < 4; ++c) {
+        double lo[2][4][5], hi[2][4][5];
+        ypass(S, i - 1 + c, j, 0.5, lo);
+        ypass(S, i - 1 + c, j + 1, -0.5, hi);
+        for (int s = 0; s < 2; ++s)
+          for (int q = 0; q < nc; ++q)
+            for (int n = 0; n <= ORD; ++n) line[c][s][q][n] = 0.5 * (lo[s][q][n] + hi[s][q][n]);
+      }
+      int fL = cell_flag(S, i, j) | cell_flag(S, i, j + 1);
+      int fR = cell_flag(S, i + 1, j) | cell_flag(S, i + 1, j + 1);
+      Deriv a[4], b[4], dL[4], dR[4];
+      second_pass(P, P.dx, line, fL, fR, a, b);
+      to_xy(nc, a, 1, dL); to_xy(nc, b, 1, dR);
+      double tc[4][5], We[4];
+      grp_point(P, 0, dL, dR, tc);
+      taylor_state(nc, tc, dt, We);
+      for (int q = 0; q < nc; ++q) WC[((size_t)(j + 1) * (nx + 1) + (i + 1)) * nc + q] = We[q];
+    }
+  // Step 5: Eq. (3.2) and Eq. (3.10).
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i)
+      for (int q = 0; q < nc; ++q) {
+        size_t o = ((size_t)q * ny + j) * nx + i;
+        auto fx = [&](int ii) { return ((size_t)j * (nx + 1) + ii) * nc + q; };
+        auto gy = [&](int jj) { return ((size_t)jj * nx + i) * nc + q; };
+        auto wc = [&](int ii, int jj) { return WC[((size_t)jj * (nx + 1) + ii) * nc + q]; };
+        Wn[o] = S.f[0][o] - dt / P.dx * (FX[fx(i + 1)] - FX[fx(i)]) -
+                dt / P.dy * (GY[gy(j + 1)] - GY[gy(j)]);
+        Vn[o] = (WX[fx(i + 1)] - WX[fx(i)]) / P.dx;
+        Yn[o] = (WY[gy(j + 1)] - WY[gy(j)]) / P.dy;
+        Zn[o] = (wc(i + 1, j + 1) - wc(i, j + 1) - wc(i + 1, j) + wc(i, j)) / (P.dx * P.dy);
+      }
+}
+
+// ----------------------------------------------------------------------------------------
+// Time step size from the CFL condition (Section 5 uses a fixed CFL number; the formula is
+// the usual maximum characteristic speed over the cell averages).
+// ----------------------------------------------------------------------------------------
+double max_rate(const Problem& P, const double* W) {
+  const size_t n = (size_t)P.nx * (P.dim == 2 ? P.ny : 1);
+  const double g = P.gamma;
+  double best = 0.0;
+  for (size_t c = 0; c < n; ++c) {
+    double r;
+    if (P.eq == EQ_BURGERS) {
+      double u = std::fabs(W[c]);
+      r = P.dim == 1 ? u / P.dx : u / P.dx + u / P.dy;
+    } else if (P.dim == 1) {
+      double rho = W[c], u = W[n + c] / rho, E = W[2 * n + c];
+      double p = (g - 1.0) * (E - 0.5 * rho * u * u);
+      r = (std::fabs(u) + std::sqrt(g * p / rho)) / P.dx;
+    } else {
+      double rho = W[c], u = W[n + c] / rho, v = W[2 * n + c] / rho, E = W[3 * n + c];
+      double p = (g - 1.0) * (E - 0.5 * rho * (u * u + v * v));
+      double cs = std::sqrt(g * p / rho);
+      r = (std::fabs(u) + cs) / P.dx + (std::fabs(v) + cs) / P.dy;
+    }
+    if (std::isnan(r)) return r;  // a non-physical state poisons the step size
+    if (r > best) best = r;
+  }
+  return best;
+}
+
+}  // namespace
+
+// ========================================================================================
+// C interface for the Python test harness (ctypes).
+// ========================================================================================
+extern "C" {
+
+typedef Problem orc_problem;
+
+// Section 2.4 reading: p1 coefficients, smoothness indicators, weights, combined polynomial.
+void orc_big_poly(const double* Wb, const double* v, double* c) { big_poly(Wb, v, c); }
+double orc_smoothness(const double* c) { return smoothness(c); }
+void orc_weights(const double* Wb, const double* v, int linear, double eps, const double* gam,
+                 double* w) { shweno_weights(Wb, v, linear, eps, gam, w); }
+void orc_recon(const double* Wb, const double* v, int linear, double eps, const double* gam,
+               double xi, double* d) {
+  double w[3], c[5];
+  shweno_weights(Wb, v, linear, eps, gam, w);
+  shweno_poly(Wb, v, w, gam, c);
+  poly_derivs(c, xi, d);
+}
+void orc_quadrature(double* lob_nodes, double* lob_w, double* gauss_nodes, double* gauss_w) {
+  lobatto4(lob_nodes, lob_w);
+  gauss3(gauss_nodes, gauss_w);
+}
+double orc_burgers_godunov(double uL, double uR) { return burgers_godunov(uL, uR); }
+void orc_hllc(const orc_problem* P, int dir, const double* WL, const double* WR, double* out) {
+  hllc_state(*P, dir, WL, WR, out);
+}
+void orc_eigen(const orc_problem* P, int dir, const double* W, double* lam, double* R, double* L) {
+  eigensystem(*P, dir, W, lam, R);
+  invert(ncomp(*P), R, L);
+}
+void orc_upwind(const orc_problem* P, int dir, const double* Ws, const double* dL,
+                const double* dR, double* out) {
+  double lam[4], R[16], L[16];
+  eigensystem(*P, dir, Ws, lam, R);
+  invert(ncomp(*P), R, L);
+  upwind(ncomp(*P), lam, R, L, dL, dR, out);
+}
+// CK on given spatial derivatives d[q][m][n] (= d^{m+n}W_q/dx^m dy^n, a 5x5 block per
+// component); returns all mixed derivatives out[q][m][n][k] = d^{m+n+k} W_q/dx^m dy^n dt^k.
+void orc_ck(const orc_problem* P, const double* d, double* out) {
+  const int nc = ncomp(*P);
+  Ser S[4];
+  for (int q = 0; q < nc; ++q) {
+    ser_zero(S[q]);
+    for (int m = 0; m <= ORD; ++m)
+      for (int n = 0; m + n <= ORD; ++n)
+        S[q].c[m][n][0] = d[(q * 5 + m) * 5 + n] / (factorial(m) * factorial(n));
+  }
+  cauchy_kovalevskaya(*P, S);
+  for (int q = 0; q < nc; ++q)
+    for (int m = 0; m <= ORD; ++m)
+      for (int n = 0; n <= ORD; ++n)
+        for (int k = 0; k <= ORD; ++k)
+          out[((q * 5 + m) * 5 + n) * 5 + k] =
+              in_range(m, n, k) ? S[q].c[m][n][k] * factorial(m) * factorial(n) * factorial(k) : 0.0;
+}
+// Steps 3-4 at one point: one-sided derivatives dL, dR as [q][m][n]; returns the time-Taylor
+// coefficients tc[q][k] = d^k W*/dt^k / k!.
+void orc_grp_point(const orc_problem* P, int dir, const double* dL, const double* dR, double* tc) {
+  Deriv a[4], b[4];
+  std::memcpy(a, dL, sizeof(Deriv) * ncomp(*P));
+  std::memcpy(b, dR, sizeof(Deriv) * ncomp(*P));
+  double t[4][5];
+  grp_point(*P, dir, a, b, t);
+  for (int q = 0; q < ncomp(*P); ++q)
+    for (int k = 0; k < 5; ++k) tc[q * 5 + k] = t[q][k];
+}
+double orc_max_rate(const orc_problem* P, const double* W) { return max_rate(*P, W); }
+
+// One step of size dt from time t.  Arrays are [comp][ny][nx] (1D: [comp][nx]); Y, Z and their
+// outputs are ignored in 1D.  flag: per-cell byte (nonzero = nonlinear weights) or null.
+void orc_step(const orc_problem* P, const double* W, const double* V, const double* Y,
+              const double* Z, const uint8_t* flag, double t, double dt, double* Wn, double* Vn,
+              double* Yn, double* Zn) {
+  State S{P, {W, V, Y, Z}, flag, t};
+  if (P->dim == 1) step1d(*P, S, dt, Wn, Vn);
+  else step2d(*P, S, dt, Wn, Vn, Yn, Zn);
+}
+
+// Runs to t_final with dt = cfl / max_rate, the last step shortened to land on t_final.
+// State arrays are updated in place.  Returns the number of steps; max_steps bounds the loop
+// (a negative return means it was hit).
+int64_t orc_run(const orc_problem* P, double* W, double* V, double* Y, double* Z,
+                const uint8_t* flag, double t_final, double cfl, int64_t max_steps, double* t_out) {
+  const size_t n = (size_t)ncomp(*P) * P->nx * (P->dim == 2 ? P->ny : 1);
+  std::vector<double> a(n), b(n), c(n), d(n);
+  double t = 0.0;
+  int64_t steps = 0;
+  while (t < t_final) {
+    if (steps >= max_steps) { *t_out = t; return -steps; }
+    double dt = cfl / max_rate(*P, W);
+    if (dt > t_final - t) dt = t_final - t;
+    orc_step(P, W, V, Y, Z, flag, t, dt, a.data(), b.data(), c.data(), d.data());
+    std::memcpy(W, a.data(), n * sizeof(double));
+    std::memcpy(V, b.data(), n * sizeof(double));
+    if (P->dim == 2) {
+      std::memcpy(Y, c.data(), n * sizeof(double));
+      std::memcpy(Z, d.data(), n * sizeof(double));
+    }
+    t += dt;
+    ++steps;
+  }
+  *t_out = t;
+  return steps;
+}
+
+}  // extern "C"

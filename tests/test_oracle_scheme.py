@@ -1,0 +1,205 @@
+"""Scheme-level pins of the oracle (Section 4 Steps 1-5 assembled).
+
+Fixed by the mathematics of the method and by the paper's printed results:
+  * conservation: periodic sums of the cell averages are constant (Eq. 2.2 / 3.2 telescope) and
+    the sums of the derivative averages vanish (Eq. 2.11 / 3.10 telescope);
+  * a constant state stays constant;
+  * design order of accuracy on the smooth problems of Examples 5.1, 5.2, 5.7, 5.8, with the
+    error magnitudes compared with Tables 5.1 and 5.2 (context: the paper omits the
+    reconstruction details, so only the order and the rough size are fixed);
+  * Sod's problem against the exact Riemann solution (first-order convergence at the jumps);
+  * a 2D run with y-independent data equals the 1D scheme; transposing a 2D problem transposes
+    the result of one step (W, V <-> Y);
+  * a reflective wall equals the mirrored periodic problem on the doubled domain.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2304_09724_gb300 import workloads as WL
+from tests import exact_riemann
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def paper_table():
+    rows = {}
+    for line in open(os.path.join(HERE, "golden", "paper_tables.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        tab, norm, n, err = line.split()
+        rows[(tab, norm, int(n))] = float(err)
+    return rows
+
+
+def problem_of(wl, **kw):
+    return O.make_problem(wl.dim, wl.eq, wl.nx, wl.ny, *wl.domain, bc=wl.bc, inflow=wl.inflow, **kw)
+
+
+def run(wl, t_final=None, **kw):
+    P = problem_of(wl, **kw)
+    st, n, t = O.run(P, wl.state, wl.t_final if t_final is None else t_final, wl.cfl)
+    assert n > 0
+    return st, n, t
+
+
+# ------------------------------------------------------------------ conservation, free stream
+@pytest.mark.parametrize("maker", [lambda: WL.burgers_sine(24), lambda: WL.euler1d_sine(24)])
+def test_conservation_1d(maker):
+    wl = maker()
+    st, n, _ = run(wl, t_final=0.3)
+    np.testing.assert_allclose(st["W"].sum(axis=-1), wl.state["W"].sum(axis=-1), rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(st["V"].sum(axis=-1), 0.0, atol=1e-11)
+
+
+def test_conservation_2d():
+    wl = WL.vortex(8)
+    P = problem_of(wl)
+    st = wl.state
+    for _ in range(2):
+        st = O.step(P, st, 0.05)
+    np.testing.assert_allclose(st["W"].sum(axis=(1, 2)), wl.state["W"].sum(axis=(1, 2)), rtol=1e-13)
+    for k in "VYZ":
+        np.testing.assert_allclose(st[k].sum(axis=(1, 2)), 0.0, atol=1e-10)
+
+
+@pytest.mark.parametrize("dim,eq,bc", [(1, WL.BURGERS, (0, 0)), (1, WL.EULER, (1, 2)), (2, WL.EULER, (0, 1, 2, 1))])
+def test_free_stream(dim, eq, bc):
+    # reflective walls keep only a state at rest in equilibrium; use zero velocity there
+    st = WL.constant_state(dim, eq, 10, 6)
+    if 2 in bc and eq == WL.EULER:
+        st["W"][1:dim + 1] = 0.0
+    P = O.make_problem(dim, eq, 10, 6, bc=bc + (0,) * (4 - len(bc)))
+    out = O.step(P, st, 0.01)
+    for k in st:
+        np.testing.assert_allclose(out[k], st[k], rtol=0, atol=1e-13)
+
+
+# ------------------------------------------------------------------ design order (Section 5)
+def l1(a, b):
+    return float(np.mean(np.abs(a - b)))
+
+
+def test_order_burgers_example_5_1():
+    tab = paper_table()
+    errs = {}
+    for n in (40, 80, 160):
+        wl = WL.burgers_sine(n)
+        st, _, _ = run(wl)
+        errs[n] = l1(st["W"][0], wl.exact(wl.t_final)[0])
+        # same size as Table 5.1 (CFL 0.6 here, 0.9 there)
+        assert 0.05 < errs[n] / tab[("5.1", "L1", n)] < 5.0
+    assert math.log2(errs[80] / errs[160]) > 4.5
+
+
+def test_order_euler1d_example_5_2():
+    tab = paper_table()
+    errs = {}
+    for n in (20, 40, 80):
+        wl = WL.euler1d_sine(n)  # T = 10 as in the paper
+        st, _, _ = run(wl)
+        errs[n] = l1(st["W"][0], wl.exact(wl.t_final)[0])
+        assert 0.1 < errs[n] / tab[("5.2", "L1", n)] < 10.0
+    assert math.log2(errs[40] / errs[80]) > 4.7
+
+
+def test_order_euler2d_example_5_7():
+    errs = {}
+    for n in (10, 20):
+        wl = WL.euler2d_sine(n)
+        st, _, _ = run(wl, t_final=0.25)
+        errs[n] = l1(st["W"][0], wl.exact(0.25)[0])
+    assert math.log2(errs[10] / errs[20]) > 4.5
+
+
+def test_order_vortex_example_5_8():
+    errs = {}
+    for n in (20, 40):
+        wl = WL.vortex(n)
+        st, _, _ = run(wl, t_final=0.25)
+        errs[n] = l1(st["W"][0], wl.exact(0.25)[0])
+    assert math.log2(errs[20] / errs[40]) > 4.0
+
+
+# ------------------------------------------------------------------ shocks
+def test_sod_against_exact_riemann_solution():
+    L, R = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    errs = {}
+    for n in (100, 200):
+        wl = WL.sod(n)
+        st, _, _ = run(wl)
+        ex = exact_riemann.density_averages(L, R, 0.0, 1.0, n, 0.5, wl.t_final)
+        rho = st["W"][0]
+        errs[n] = l1(rho, ex)
+        assert rho.min() > 0.125 * 0.97 and rho.max() < 1.0 * 1.03  # no large over/undershoot
+    assert errs[200] < 0.75 * errs[100]
+    assert errs[200] < 4e-3
+
+
+# ------------------------------------------------------------------ dimensional consistency
+def test_2d_with_y_independent_data_equals_1d():
+    wl1 = WL.euler1d_sine(16)
+    W1, V1 = wl1.state["W"], wl1.state["V"]
+    ny = 5
+    W2 = np.zeros((4, ny, 16))
+    V2 = np.zeros((4, ny, 16))
+    for q2, q1 in ((0, 0), (1, 1), (3, 2)):
+        W2[q2] = W1[q1][None]
+        V2[q2] = V1[q1][None]
+    st2 = {"W": W2, "V": V2, "Y": np.zeros_like(W2), "Z": np.zeros_like(W2)}
+    P1 = O.make_problem(1, WL.EULER, 16, x0=0.0, x1=2.0)
+    P2 = O.make_problem(2, WL.EULER, 16, ny, 0.0, 2.0, 0.0, 1.0)
+    s1, s2 = wl1.state, st2
+    for _ in range(3):
+        s1 = O.step(P1, s1, 0.02)
+        s2 = O.step(P2, s2, 0.02)
+    for q2, q1 in ((0, 0), (1, 1), (3, 2)):
+        for j in range(ny):
+            np.testing.assert_allclose(s2["W"][q2, j], s1["W"][q1], rtol=1e-12, atol=1e-13)
+            np.testing.assert_allclose(s2["V"][q2, j], s1["V"][q1], rtol=1e-10, atol=1e-11)
+    np.testing.assert_allclose(s2["W"][2], 0.0, atol=1e-13)
+    np.testing.assert_allclose(s2["Y"], 0.0, atol=1e-11)
+
+
+def test_transposition_symmetry_one_step():
+    """Swapping x and y (and the two momenta) swaps F with G and V with Y; one step commutes
+    with the swap for W, V and Y (the corner values of Z use x-direction problems only)."""
+    nx, ny = 7, 9
+    W, V, Y, Z = WL.random_smooth_2d(3, nx, ny)
+    P = O.make_problem(2, WL.EULER, nx, ny, 0.0, 1.0, 0.0, 1.0)
+    Pt = O.make_problem(2, WL.EULER, ny, nx, 0.0, 1.0, 0.0, 1.0)
+    sw = [0, 2, 1, 3]
+    tr = lambda a: np.ascontiguousarray(np.transpose(a[sw], (0, 2, 1)))
+    a = O.step(P, {"W": W, "V": V, "Y": Y, "Z": Z}, 0.01)
+    b = O.step(Pt, {"W": tr(W), "V": tr(Y), "Y": tr(V), "Z": tr(Z)}, 0.01)
+    np.testing.assert_allclose(tr(a["W"]), b["W"], rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(tr(a["V"]), b["Y"], rtol=1e-10, atol=1e-11)
+    np.testing.assert_allclose(tr(a["Y"]), b["V"], rtol=1e-10, atol=1e-11)
+
+
+def test_reflective_wall_equals_mirrored_periodic_problem():
+    n = 12
+    W, V = WL.random_smooth_1d(2, n)
+    W[1] -= W[1].mean()  # any momentum is fine; the mirror flips it
+    # doubled periodic domain: mirror image on the left of the original cells
+    Wd = np.concatenate([W[:, ::-1] * np.array([1, -1, 1])[:, None], W], axis=1)
+    Vd = np.concatenate([V[:, ::-1] * np.array([-1, 1, -1])[:, None], V], axis=1)
+    Pr = O.make_problem(1, WL.EULER, n, x0=0.0, x1=1.0, bc=(WL.REFLECTIVE, WL.REFLECTIVE))
+    # right wall of the reflective problem sits at x = 1, whose mirror is the doubled domain's
+    # periodic seam: (-1, 1) periodic with the image on (-1, 0)
+    Pp = O.make_problem(1, WL.EULER, 2 * n, x0=-1.0, x1=1.0, bc=(WL.PERIODIC, WL.PERIODIC))
+    a = O.step(Pr, {"W": W, "V": V}, 0.004)
+    b = O.step(Pp, {"W": Wd, "V": Vd}, 0.004)
+    np.testing.assert_allclose(a["W"], b["W"][:, n:], rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(a["V"], b["V"][:, n:], rtol=1e-10, atol=1e-11)
+
+
+def test_dmr_small_runs_and_stays_physical():
+    wl = WL.dmr(32, 8)
+    P = problem_of(wl)
+    st, n, t = O.run(P, wl.state, 0.002, 0.6)
+    rho = st["W"][0]
+    assert np.isfinite(st["W"]).all() and rho.min() > 0
