@@ -1,0 +1,277 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the ADER-SHWENO step on a GB300: 2D Euler isentropic vortex
+(Example 5.8: strength 5, centre (5,5), periodic (0,10)^2, mean state rho = u = v = p = 1),
+2048 x 2048 cells, FP64, CFL 0.6.  One benchmark step = one time step of the whole path
+(SHWENO reconstruction, HLLC + derivative Riemann problems, Cauchy-Kovalevskaya, Lobatto flux,
+update of W, V, Y, Z, fused CFL reduction for the next step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--n 2048]
+
+Prints one JSON line (rank 0).  Metric: cell-updates/s (whole job).  For N > 1 (torchrun, one
+process per GPU) every rank advances its own replica of the mesh ("replicas only": one mesh
+needs no exchange on one GPU), and value = all ranks' cell-updates / max-over-ranks time.
+--impl reference times the oracle (plain single-threaded C++) on the host cores instead, on a
+bounded window of the same mesh per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CFL = 0.6
+# FP64 peak derived from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP64_MEASURED_TFLOPS = 1.1935  # DFMA microbenchmark on this machine's GB300 (all SMs busy)
+# FP64 operations (DFMA counted as 2) per face point of the face kernels, from the ncu
+# instruction counters of the committed kernels; None until measured.
+FLOPS_PER_XFACE_POINT = None
+BYTES_PER_CELL_UPDATE = 256  # 16 doubles read + 16 written per cell (ideal reuse)
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except Exception:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k] and "Not" not in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample(wl, window, steps):
+    """Times the oracle (single-threaded C++) on a window x window block of the mesh, `steps`
+    times; returns (cell-updates/s, seconds)."""
+    from oracle import oracle as O
+
+    P = O.make_problem(2, wl.eq, wl.nx, wl.ny, *wl.domain, bc=wl.bc)
+    dt = CFL / O.max_rate(P, wl.state["W"])
+    i0 = wl.nx // 2 - window // 2
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        O.step2d_window(P, wl.state, dt, i0, i0, window, window)
+    el = time.perf_counter() - t0
+    return window * window * steps / el, el
+
+
+def bench_reference(args):
+    """Reference arm: the oracle on the host cores (rank 0 only)."""
+    world, rank, _ = dist_init()
+    if rank != 0:
+        return
+    from paper_2304_09724_gb300 import workloads as WL
+
+    wl = WL.vortex(args.n)
+    win = args.ref_window
+    oracle_sample(wl, win, args.warmup)
+    rate, el = oracle_sample(wl, win, args.steps)
+    line = {
+        "impl": "reference", "metric": "2D Euler cell-updates/s", "value": rate, "unit": "cell-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"isentropic vortex {args.n}x{args.n}, FP64, CFL {CFL}",
+                   "sample": f"{win}x{win}-cell window of the {args.n}^2 mesh per step"},
+        "cpu_baseline": {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps of a {win}x{win}-cell window"},
+        "e2e": {"value": rate, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def bench_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2304_09724_gb300 import shweno as S
+    from paper_2304_09724_gb300 import workloads as WL
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    barrier = (lambda: __import__("torch.distributed").distributed.barrier()) if world > 1 else (lambda: None)
+
+    n = args.n
+    wl = WL.vortex(n)
+    cells = wl.nx * wl.ny
+    stream = torch.cuda.Stream()
+    sol = S.Solver(2, S.EULER, n, n, wl.domain, wl.bc, stream=stream.cuda_stream)
+    dev = {k: torch.from_numpy(v).cuda() for k, v in wl.state.items()}
+    sol.set_state(dev)
+    torch.cuda.synchronize()
+
+    # warm-up (W >= 3 steps), then K timed steps with per-kernel events
+    S.shweno_advance(sol.h, args.warmup, CFL)
+    S.shweno_sync(sol.h)
+    S.shweno_set_timing(sol.h, True)
+    S.shweno_get_timing(sol.h)  # clear
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        S.shweno_advance(sol.h, args.steps, CFL)
+        e1.record(stream)
+        S.shweno_sync(sol.h)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    kernel_ms, timed_steps = S.shweno_get_timing(sol.h)
+    S.shweno_set_timing(sol.h, False)
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+    sec = ms / 1000.0
+    value = world * cells * args.steps / sec
+
+    # end to end through the C ABI with host buffers: per step, copy the state in from pinned
+    # host memory, take one CFL step, copy the state out
+    host_in = {k: torch.from_numpy(v).pin_memory() for k, v in wl.state.items()}
+    host_out = {k: torch.empty_like(v).pin_memory() for k, v in host_in.items()}
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        S.shweno_set_state(sol.h, host_in["W"], host_in["V"], host_in["Y"], host_in["Z"], 0.0)
+        S.shweno_advance(sol.h, 1, CFL)
+        S.shweno_get_state(sol.h, host_out["W"], host_out["V"], host_out["Y"], host_out["Z"])
+    e2e_sec = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([e2e_sec], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_sec = float(t.item())
+    state_bytes = sum(v.numel() * 8 for v in host_in.values())
+    assert np.isfinite(host_out["W"].numpy()).all()
+    sol.close()
+
+    if rank != 0:
+        return
+    pk = peaks()
+    total_k = sum(kernel_ms.values())
+    dom = max(kernel_ms, key=kernel_ms.get)
+    dom_ms = kernel_ms[dom] / max(timed_steps, 1)
+    # x-face kernel: (n+1) faces x n rows x 3 Gauss points + (n+1)^2 corner points per launch
+    xpoints = 3 * (n + 1) * n + (n + 1) * (n + 1)
+    roof = None
+    if dom == "xface2d" and FLOPS_PER_XFACE_POINT:
+        flops = FLOPS_PER_XFACE_POINT * xpoints
+        ach = flops / (dom_ms / 1000.0) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe)"}
+    hbm_gbs = cells * BYTES_PER_CELL_UPDATE / (sec / (world * args.steps)) / 1e9 / world
+    line = {
+        "metric": "2D Euler cell-updates/s", "value": value, "unit": "cell-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"2D Euler isentropic vortex {n}x{n} (Example 5.8), FP64, CFL {CFL}, plain (nonlinear weights)",
+                   "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (state 2x537 MB, step scratch 3 GB)"},
+        "roofline": roof,
+        "kernels_ms_per_step": {k: v / max(timed_steps, 1) for k, v in kernel_ms.items()},
+        "dominant_kernel_share": kernel_ms[dom] / total_k if total_k else None,
+        "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": pk.get("hbm_gbs", 6750.0),
+                "frac": hbm_gbs / pk.get("hbm_gbs", 6750.0), "bytes_per_cell_update": BYTES_PER_CELL_UPDATE},
+        "clocks": clocks,
+        "e2e": {"value": world * cells * e2e_steps / e2e_sec, "unit": "cell-updates/s",
+                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
+        "gpu_launches": 3 + 6 * args.steps,
+    }
+    if not args.no_cpu_baseline:
+        rate, el = oracle_sample(wl, args.cpu_window, 1)
+        line["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one step of a {args.cpu_window}x{args.cpu_window}-cell window of the {n}^2 mesh ({el:.1f} s)"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--cpu-window", type=int, default=160)
+    ap.add_argument("--ref-window", type=int, default=48)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * shweno.h -- C ABI of the GB300 (sm_103a) FP64 library for the one-stage ADER-SHWENO scheme
+ * of Luo, Li, Qiu, Zhu and Chen, "A compact simple HWENO scheme with ADER time discretization
+ * for hyperbolic conservation laws I: structured meshes" (arXiv 2304.09724).
+ *
+ * Problem (Section 2, Eq. 2.1; Section 3, Eq. 3.1): W_t + F(W)_x (+ G(W)_y) = 0 on a uniform
+ * Cartesian mesh, for scalar Burgers (F = G = W^2/2) or the compressible Euler equations of an
+ * ideal gas (Eq. 5.1, 5.2; E = p/(gamma-1) + rho |u|^2/2).  The state of the method is, per cell,
+ * the cell average W, the cell average V of W_x and, in 2D, the averages Y of W_y and Z of W_xy
+ * (Section 2.5 Eq. 2.10; Section 3.2 Eq. 3.9).  One step is Section 4, Steps 1-5: SHWENO
+ * reconstruction, Lax-Wendroff (Cauchy-Kovalevskaya) procedure, leading term and derivative
+ * Riemann problems, Lobatto-in-time flux, update of W (Eq. 2.2 / 3.2) and of V, Y, Z
+ * (Eq. 2.11 / 3.10).
+ *
+ * Layout of every state array: float64, component-major, x fastest, no ghost cells:
+ *   1D: [ncomp][nx]          2D: [ncomp][ny][nx]
+ * ncomp = 1 (Burgers), 3 (1D Euler: rho, rho u, E), 4 (2D Euler: rho, rho u, rho v, E).
+ *
+ * Conventions for every call:
+ *  - Every call returns a shweno_status; nothing throws across the ABI.  On error the handle's
+ *    message is available through shweno_last_error().
+ *  - Pointers marked "device" must be device memory of the handle's GPU; "host" pointers are
+ *    ordinary host memory.  Copies are ordered on the handle's CUDA stream; calls that return
+ *    data to the host synchronise that stream.
+ *  - The library owns its device buffers (two state buffers and the step scratch); callers keep
+ *    ownership of everything they pass in.
+ *  - One thread at a time per handle.
+ */
+#ifndef SHWENO_H
+#define SHWENO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SHWENO_OK = 0,
+  SHWENO_E_INVALID = 1,      /* bad argument; nothing was changed */
+  SHWENO_E_CUDA = 2,         /* a CUDA call failed; message in shweno_last_error() */
+  SHWENO_E_NOMEM = 3,        /* device allocation failed */
+  SHWENO_E_NONPHYSICAL = 4,  /* a step produced rho <= 0, p <= 0 or a NaN; that step was not
+                                committed: the state and time are those before it */
+  SHWENO_E_TIMEOUT = 5,      /* a bounded device-side wait gave up (batched runs) */
+  SHWENO_E_STATE = 6         /* call not valid in the handle's current state */
+} shweno_status;
+
+typedef enum { SHWENO_BURGERS = 0, SHWENO_EULER = 1 } shweno_eq;
+
+/* Boundary conditions (Section 5 examples).  Ghost cells are never stored; they are mapped
+ * on load.  OUTFLOW copies every cell quantity of the boundary cell (zero-order extrapolation,
+ * the "non-reflecting"/outflow sides of Examples 5.3, 5.9, 5.10).  REFLECTIVE mirrors the
+ * state with the normal momentum and the derivatives normal to the wall changing sign
+ * (Example 5.6).  INFLOW imposes the conserved state inflow[side] with zero derivatives.
+ * DMR_BOTTOM / DMR_TOP are the lower and upper sides of the double Mach reflection problem
+ * (Example 5.10): exact post-shock state for x < 1/6 and a wall beyond; exact position of the
+ * Mach 10 shock at the current time, sampled at ghost-cell centres. */
+typedef enum {
+  SHWENO_BC_PERIODIC = 0,
+  SHWENO_BC_OUTFLOW = 1,
+  SHWENO_BC_REFLECTIVE = 2,
+  SHWENO_BC_INFLOW = 3,
+  SHWENO_BC_DMR_BOTTOM = 4,
+  SHWENO_BC_DMR_TOP = 5
+} shweno_bc_kind;
+
+typedef struct {
+  int32_t dim;        /* 1 or 2 */
+  int32_t eq;         /* shweno_eq */
+  int64_t nx, ny;     /* cells per direction (ny ignored in 1D); each >= 4 */
+  double x0, x1;      /* domain [x0, x1] */
+  double y0, y1;      /* domain [y0, y1] (2D) */
+} shweno_grid;
+
+typedef struct {
+  int32_t kind[4];        /* shweno_bc_kind for x-low, x-high, y-low, y-high */
+  double inflow[4][4];    /* conserved state of an INFLOW side, by side */
+} shweno_bc;
+
+/* Reconstruction options.  Defaults (opts == NULL): nonlinear weights everywhere,
+ * eps = 1e-6, linear weights gamma = (0.994, 0.003, 0.003) (Section 2.4). */
+typedef struct {
+  int32_t flag_mode;  /* 0: nonlinear weights in every cell; 1: linear weights in every cell;
+                         2: per-cell troubled flags (shweno_set_flags) */
+  double eps;         /* epsilon of the nonlinear weights */
+  double gam[3];      /* linear weights, positive, summing to 1 */
+} shweno_opts;
+
+typedef struct shweno_handle shweno_handle;
+
+/* Creates a solver for one mesh on the current CUDA device.  gamma: ratio of specific heats
+ * (Euler; ignored for Burgers).  cuda_stream: a cudaStream_t on which every operation of the
+ * handle is ordered; NULL makes the handle create its own stream (one that synchronises with the
+ * legacy default stream).  The initial state is zero, t = 0.
+ * Errors: INVALID (bad grid, BC or options), NOMEM, CUDA. */
+shweno_status shweno_create(const shweno_grid* grid, double gamma, const shweno_bc* bc,
+                            const shweno_opts* opts, void* cuda_stream, shweno_handle** out);
+
+/* Copies a state in (W, V and, in 2D, Y, Z; each [ncomp][ny][nx]).  on_device = 1: device
+ * pointers, 0: host pointers.  Sets the time to t and the step count to 0.
+ * Errors: INVALID (null pointer), CUDA. */
+shweno_status shweno_set_state(shweno_handle* h, const double* W, const double* V,
+                               const double* Y, const double* Z, double t, int on_device);
+
+/* Copies the committed state out (same layouts; Y, Z ignored in 1D).  Synchronises. */
+shweno_status shweno_get_state(shweno_handle* h, double* W, double* V, double* Y, double* Z,
+                               int on_device);
+
+/* One step of size dt > 0 from the current time (Section 4 Steps 1-5).  Synchronises to check
+ * the new state; NONPHYSICAL leaves the state and time of before the step. */
+shweno_status shweno_step(shweno_handle* h, double dt);
+
+/* Advances to t_final with dt = cfl / max over cells of the characteristic rate
+ * ((|u|+c)/dx + (|v|+c)/dy; Burgers |u| instead of |u|+c), the last step shortened to land on
+ * t_final.  The step size is computed and applied on the device (CUDA graph of several steps);
+ * the host only polls for completion.  t_out / nsteps_out (may be NULL) receive the final time
+ * and the number of steps taken by this call.  NONPHYSICAL: stops at the last good state. */
+shweno_status shweno_run(shweno_handle* h, double t_final, double cfl, double* t_out,
+                         int64_t* nsteps_out);
+
+/* Enqueues exactly nsteps CFL steps (dt = cfl / rate, no end time) and returns without waiting.
+ * A non-physical step stops the sequence on the device (the last good state stays committed);
+ * the error is reported by the next shweno_sync.  Used for throughput measurement. */
+shweno_status shweno_advance(shweno_handle* h, int64_t nsteps, double cfl);
+
+/* Waits for the handle's stream; returns NONPHYSICAL if a step since the last call failed. */
+shweno_status shweno_sync(shweno_handle* h);
+
+/* Per-kernel timing (profiling).  While enabled, every step records CUDA events on the handle's
+ * stream around each of its kernels (steps are then launched one by one instead of as a graph).
+ * shweno_get_timing synchronises, writes the accumulated milliseconds of kernel k to ms[k]
+ * (k < max_kernels), the kernel count to *nkernels and the number of timed steps to *nsteps, and
+ * clears the totals.  shweno_kernel_name(h, k) names kernel k of the handle's step. */
+shweno_status shweno_set_timing(shweno_handle* h, int enable);
+shweno_status shweno_get_timing(shweno_handle* h, double* ms, int max_kernels, int* nkernels,
+                                int64_t* nsteps);
+const char* shweno_kernel_name(const shweno_handle* h, int k);
+
+/* Step size the CFL rule would take now: dt = cfl / rate (rate_out may be NULL). */
+shweno_status shweno_cfl_dt(shweno_handle* h, double cfl, double* dt_out, double* rate_out);
+
+/* Current time and committed step count. */
+shweno_status shweno_get_time(shweno_handle* h, double* t_out, int64_t* nsteps_out);
+
+/* Per-cell troubled flags for flag_mode 2 ([ny][nx] bytes, nonzero = nonlinear weights;
+ * device or host pointer).  A reconstruction anchored on a cell with flag 0 uses the linear
+ * weights, which makes it exactly the big-stencil polynomial p1. */
+shweno_status shweno_set_flags(shweno_handle* h, const uint8_t* flags, int on_device);
+
+shweno_status shweno_destroy(shweno_handle* h);
+
+/* Message of the last failed call on h ("" if none); h may be NULL for create errors. */
+const char* shweno_last_error(const shweno_handle* h);
+
+/* Device allocation hook: every device buffer of every handle created afterwards comes from
+ * alloc(bytes, ctx) and goes back through release(ptr, ctx).  NULL restores cudaMalloc/cudaFree.
+ * alloc returns NULL on failure (create then fails with NOMEM). */
+typedef void* (*shweno_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*shweno_free_fn)(void* ptr, void* ctx);
+shweno_status shweno_set_allocator(shweno_alloc_fn alloc, shweno_free_fn release, void* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHWENO_H */

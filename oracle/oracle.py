@@ -74,7 +74,11 @@ def lib():
         L.orc_step.argtypes = [pp, dp, dp, dp, dp, u8p, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
         L.orc_run.argtypes = [pp, dp, dp, dp, dp, u8p, ctypes.c_double, ctypes.c_double,
                               ctypes.c_int64, dp]
+        L.orc_step2d_cells.argtypes = [pp, dp, dp, dp, dp, u8p, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, ctypes.POINTER(ctypes.c_int32), dp]
         L.orc_run.restype = ctypes.c_int64
+        L.orc_step2d_window.argtypes = [pp, dp, dp, dp, dp, u8p, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
         _lib = L
     return _lib
 
@@ -209,6 +213,29 @@ def step(P, state, dt, t=0.0, flag=None):
     if P.dim == 2:
         out["Y"], out["Z"] = Yn, Zn
     return out
+
+
+def step2d_cells(P, state, dt, cells, t=0.0, flag=None):
+    """One 2D step evaluated only at the listed (i, j) cells.  Returns {'W','V','Y','Z'}: [n][nc]."""
+    W, V, Y, Z = (_f64(state[k]) for k in "WVYZ")
+    ij = np.ascontiguousarray(np.asarray(cells, dtype=np.int32).reshape(-1, 2))
+    n, nc = len(ij), ncomp(P)
+    out = np.zeros((n, 4, nc))
+    fl, fp = _flag_ptr(flag)
+    lib().orc_step2d_cells(ctypes.byref(P), _dp(W), _dp(V), _dp(Y), _dp(Z), fp, t, dt, n,
+                           ij.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(out))
+    return {k: out[:, f, :] for f, k in enumerate("WVYZ")}
+
+
+def step2d_window(P, state, dt, i0, j0, w, h, t=0.0, flag=None):
+    """One 2D step evaluated on the window [i0, i0+w) x [j0, j0+h).  Returns {'W',...}: [nc][h][w]."""
+    W, V, Y, Z = (_f64(state[k]) for k in "WVYZ")
+    nc = ncomp(P)
+    out = np.zeros((4, nc, h, w))
+    fl, fp = _flag_ptr(flag)
+    lib().orc_step2d_window(ctypes.byref(P), _dp(W), _dp(V), _dp(Y), _dp(Z), fp, t, dt, i0, j0, w, h,
+                            _dp(out))
+    return {k: out[f] for f, k in enumerate("WVYZ")}
 
 
 def run(P, state, t_final, cfl, flag=None, max_steps=10 ** 9):

@@ -300,9 +300,14 @@ void hllc_state(const Problem& P, int dir, const double* WL, const double* WR, d
 // ----------------------------------------------------------------------------------------
 // Step 3b: linearised Riemann problems for the derivatives, Eq. (2.8) / (3.7).  With
 // A = F'(W*) = R diag(lambda) L the solution at x/t = 0 is R (H o L d_L + (1-H) o L d_R) where
-// H = 1 for lambda > 0, 0 for lambda < 0 and 1/2 for lambda = 0 (the average of both sides).
+// H = 1 for lambda > 0, 0 for lambda < 0 and 1/2 for a standing wave (the average of both
+// sides).  A wave counts as standing when |lambda| <= 1e-12 * scale (scale: the sound speed of
+// W*, or for Burgers the larger face speed), so that a speed that is zero in exact arithmetic
+// (the normal velocity at a reflective wall) is not decided by rounding.
 // Right eigenvectors of the Euler Jacobian (Toro, Section 3.2), L = R^{-1} by elimination.
 // ----------------------------------------------------------------------------------------
+const double STANDING_WAVE_TOL = 1e-12;
+
 void eigensystem(const Problem& P, int dir, const double* W, double* lam, double* R) {
   const int nc = ncomp(P);
   if (P.eq == EQ_BURGERS) { lam[0] = W[0]; R[0] = 1.0; return; }
@@ -336,13 +341,14 @@ void eigensystem(const Problem& P, int dir, const double* W, double* lam, double
     for (int q = 0; q < 4; ++q) R[q * 4 + k] = r[k][q];
 }
 
-void upwind(int nc, const double* lam, const double* R, const double* L, const double* dL,
-            const double* dR, double* out) {
+void upwind(int nc, const double* lam, double scale, const double* R, const double* L,
+            const double* dL, const double* dR, double* out) {
   double a[4];
+  const double tol = STANDING_WAVE_TOL * scale;
   for (int k = 0; k < nc; ++k) {
     double aL = 0.0, aR = 0.0;
     for (int q = 0; q < nc; ++q) { aL += L[k * nc + q] * dL[q]; aR += L[k * nc + q] * dR[q]; }
-    double H = lam[k] > 0.0 ? 1.0 : (lam[k] < 0.0 ? 0.0 : 0.5);
+    double H = lam[k] > tol ? 1.0 : (lam[k] < -tol ? 0.0 : 0.5);
     a[k] = H * aL + (1.0 - H) * aR;
   }
   for (int q = 0; q < nc; ++q) {
@@ -350,6 +356,17 @@ void upwind(int nc, const double* lam, const double* R, const double* L, const d
     for (int k = 0; k < nc; ++k) s += R[q * nc + k] * a[k];
     out[q] = s;
   }
+}
+
+// Speed scale of the standing-wave test: sound speed of W* (Euler), max |u| of the face states
+// (Burgers).
+double wave_scale(const Problem& P, const double* Ws, double uL, double uR) {
+  if (P.eq == EQ_BURGERS) return std::fmax(std::fabs(uL), std::fabs(uR));
+  const int nc = ncomp(P);
+  double rho = Ws[0], ke = 0.0;
+  for (int q = 1; q < nc - 1; ++q) ke += 0.5 * Ws[q] * Ws[q] / rho;
+  double p = (P.gamma - 1.0) * (Ws[nc - 1] - ke);
+  return std::sqrt(P.gamma * p / rho);
 }
 
 // ----------------------------------------------------------------------------------------
@@ -477,6 +494,7 @@ void grp_point(const Problem& P, int dir, const Deriv* dL, const Deriv* dR, doub
   double lam[4], R[16], L[16];
   eigensystem(P, dir, Ws, lam, R);
   invert(nc, R, L);
+  const double scale = wave_scale(P, Ws, WL[0], WR[0]);
   Ser S[4];
   for (int q = 0; q < nc; ++q) { ser_zero(S[q]); S[q].c[0][0][0] = Ws[q]; }
   const int nmax = P.dim == 2 ? ORD : 0;
@@ -485,7 +503,7 @@ void grp_point(const Problem& P, int dir, const Deriv* dL, const Deriv* dR, doub
       if (m == 0 && n == 0) continue;
       double a[4], b[4], o[4];
       for (int q = 0; q < nc; ++q) { a[q] = dL[q][m][n]; b[q] = dR[q][m][n]; }
-      upwind(nc, lam, R, L, a, b, o);
+      upwind(nc, lam, scale, R, L, a, b, o);
       for (int q = 0; q < nc; ++q) S[q].c[m][n][0] = o[q] / (factorial(m) * factorial(n));
     }
   cauchy_kovalevskaya(P, S);
@@ -720,92 +738,176 @@ void to_xy(int nc, const Deriv* in, int normal_is_x, Deriv* out) {
       }
 }
 
+// Time-averaged flux F-hat (Eq. 3.3 with the Gauss sum of Eq. 3.8) and Gauss-weighted state
+// at t_{n+1} (the sum in Eq. 3.10) of the x-face (i+1/2, j).
+void xface(const State& S, int i, int j, double dt, double* Fs, double* Ws) {
+  const Problem& P = *S.P;
+  const int nc = ncomp(P);
+  double gs[3], gw[3];
+  gauss3(gs, gw);
+  for (int q = 0; q < nc; ++q) Fs[q] = Ws[q] = 0.0;
+  for (int g = 0; g < 3; ++g) {
+    double line[4][2][4][5];
+    for (int c = 0; c < 4; ++c) ypass(S, i - 1 + c, j, gs[g], line[c]);
+    Deriv a[4], b[4], dL[4], dR[4];
+    second_pass(P, P.dx, line, cell_flag(S, i, j), cell_flag(S, i + 1, j), a, b);
+    to_xy(nc, a, 1, dL); to_xy(nc, b, 1, dR);
+    double tc[4][5], F[4], We[4];
+    grp_point(P, 0, dL, dR, tc);
+    ader_flux(P, 0, tc, dt, F, We);
+    for (int q = 0; q < nc; ++q) { Fs[q] += gw[g] * F[q]; Ws[q] += gw[g] * We[q]; }
+  }
+}
+// Same for the y-face (i, j+1/2), Eq. (3.4).
+void yface(const State& S, int i, int j, double dt, double* Gs, double* Ws) {
+  const Problem& P = *S.P;
+  const int nc = ncomp(P);
+  double gs[3], gw[3];
+  gauss3(gs, gw);
+  for (int q = 0; q < nc; ++q) Gs[q] = Ws[q] = 0.0;
+  for (int g = 0; g < 3; ++g) {
+    double line[4][2][4][5];
+    for (int c = 0; c < 4; ++c) xpass(S, i, j - 1 + c, gs[g], line[c]);
+    Deriv a[4], b[4], dB[4], dT[4];
+    second_pass(P, P.dy, line, cell_flag(S, i, j), cell_flag(S, i, j + 1), a, b);
+    to_xy(nc, a, 0, dB); to_xy(nc, b, 0, dT);
+    double tc[4][5], G[4], We[4];
+    grp_point(P, 1, dB, dT, tc);
+    ader_flux(P, 1, tc, dt, G, We);
+    for (int q = 0; q < nc; ++q) { Gs[q] += gw[g] * G[q]; Ws[q] += gw[g] * We[q]; }
+  }
+}
+// State at t_{n+1} at the corner (i+1/2, j+1/2): the y-direction traces of rows j (eta = +1/2)
+// and j+1 (eta = -1/2) are averaged, then one x-direction generalised Riemann problem is solved
+// and evaluated at tau = dt (the paper says only "in a similar way", end of Section 3.3).
+void corner(const State& S, int i, int j, double dt, double* We) {
+  const Problem& P = *S.P;
+  const int nc = ncomp(P);
+  double line[4][2][4][5];
+  for (int c = 0; c < 4; ++c) {
+    double lo[2][4][5], hi[2][4][5];
+    ypass(S, i - 1 + c, j, 0.5, lo);
+    ypass(S, i - 1 + c, j + 1, -0.5, hi);
+    for (int s = 0; s < 2; ++s)
+      for (int q = 0; q < nc; ++q)
+        for (int n = 0; n <= ORD; ++n) line[c][s][q][n] = 0.5 * (lo[s][q][n] + hi[s][q][n]);
+  }
+  int fL = cell_flag(S, i, j) | cell_flag(S, i, j + 1);
+  int fR = cell_flag(S, i + 1, j) | cell_flag(S, i + 1, j + 1);
+  Deriv a[4], b[4], dL[4], dR[4];
+  second_pass(P, P.dx, line, fL, fR, a, b);
+  to_xy(nc, a, 1, dL); to_xy(nc, b, 1, dR);
+  double tc[4][5];
+  grp_point(P, 0, dL, dR, tc);
+  taylor_state(nc, tc, dt, We);
+}
+
+// Step 5 for one cell from its four faces and four corners: Eq. (3.2) and Eq. (3.10).
+void update_cell(const State& S, int i, int j, double dt, const double Fx[2][4], const double Wx[2][4],
+                 const double Gy[2][4], const double Wy[2][4], const double Wc[2][2][4],
+                 double* Wn, double* Vn, double* Yn, double* Zn) {
+  const Problem& P = *S.P;
+  const int nc = ncomp(P);
+  for (int q = 0; q < nc; ++q) {
+    size_t o = ((size_t)q * P.ny + j) * P.nx + i;
+    Wn[q] = S.f[0][o] - dt / P.dx * (Fx[1][q] - Fx[0][q]) - dt / P.dy * (Gy[1][q] - Gy[0][q]);
+    Vn[q] = (Wx[1][q] - Wx[0][q]) / P.dx;
+    Yn[q] = (Wy[1][q] - Wy[0][q]) / P.dy;
+    Zn[q] = (Wc[1][1][q] - Wc[1][0][q] - Wc[0][1][q] + Wc[0][0][q]) / (P.dx * P.dy);
+  }
+}
+
 void step2d(const Problem& P, const State& S, double dt, double* Wn, double* Vn, double* Yn,
             double* Zn) {
   const int nc = ncomp(P), nx = P.nx, ny = P.ny;
-  double gs[3], gw[3];
-  gauss3(gs, gw);
-  // x-faces (i+1/2, j), i = -1..nx-1: F-hat and the Gauss-weighted state at t_{n+1}.
+  // every face and corner once, then the cell updates
   std::vector<double> FX((size_t)(nx + 1) * ny * nc), WX((size_t)(nx + 1) * ny * nc);
   std::vector<double> GY((size_t)nx * (ny + 1) * nc), WY((size_t)nx * (ny + 1) * nc);
   std::vector<double> WC((size_t)(nx + 1) * (ny + 1) * nc);
   for (int j = 0; j < ny; ++j)
     for (int i = -1; i < nx; ++i) {
-      double Fs[4] = {0}, Ws[4] = {0};
-      for (int g = 0; g < 3; ++g) {
-        double line[4][2][4][5];
-        for (int c = 0; c < 4; ++c) ypass(S, i - 1 + c, j, gs[g], line[c]);
-        Deriv a[4], b[4], dL[4], dR[4];
-        second_pass(P, P.dx, line, cell_flag(S, i, j), cell_flag(S, i + 1, j), a, b);
-        to_xy(nc, a, 1, dL); to_xy(nc, b, 1, dR);
-        double tc[4][5], F[4], We[4];
-        grp_point(P, 0, dL, dR, tc);
-        ader_flux(P, 0, tc, dt, F, We);
-        for (int q = 0; q < nc; ++q) { Fs[q] += gw[g] * F[q]; Ws[q] += gw[g] * We[q]; }
-      }
-      for (int q = 0; q < nc; ++q) {
-        size_t o = ((size_t)j * (nx + 1) + (i + 1)) * nc + q;
-        FX[o] = Fs[q]; WX[o] = Ws[q];
-      }
+      size_t o = ((size_t)j * (nx + 1) + (i + 1)) * nc;
+      xface(S, i, j, dt, &FX[o], &WX[o]);
     }
-  // y-faces (i, j+1/2), j = -1..ny-1.
   for (int j = -1; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
-      double Gs[4] = {0}, Ws[4] = {0};
-      for (int g = 0; g < 3; ++g) {
-        double line[4][2][4][5];
-        for (int c = 0; c < 4; ++c) xpass(S, i, j - 1 + c, gs[g], line[c]);
-        Deriv a[4], b[4], dB[4], dT[4];
-        second_pass(P, P.dy, line, cell_flag(S, i, j), cell_flag(S, i, j + 1), a, b);
-        to_xy(nc, a, 0, dB); to_xy(nc, b, 0, dT);
-        double tc[4][5], G[4], We[4];
-        grp_point(P, 1, dB, dT, tc);
-        ader_flux(P, 1, tc, dt, G, We);
-        for (int q = 0; q < nc; ++q) { Gs[q] += gw[g] * G[q]; Ws[q] += gw[g] * We[q]; }
-      }
-      for (int q = 0; q < nc; ++q) {
-        size_t o = ((size_t)(j + 1) * nx + i) * nc + q;
-        GY[o] = Gs[q]; WY[o] = Ws[q];
-      }
+      size_t o = ((size_t)(j + 1) * nx + i) * nc;
+      yface(S, i, j, dt, &GY[o], &WY[o]);
     }
-  // Corners (i+1/2, j+1/2): the y-direction traces of rows j (eta = +1/2) and j+1 (eta = -1/2)
-  // are averaged, then one x-direction generalised Riemann problem is solved and evaluated at
-  // tau = dt ("in a similar way", Section 3.3).
   for (int j = -1; j < ny; ++j)
-    for (int i = -1; i < nx; ++i) {
-      double line[4][2][4][5];
-      for (int c = 0; c < 4; ++c) {
-        double lo[2][4][5], hi[2][4][5];
-        ypass(S, i - 1 + c, j, 0.5, lo);
-        ypass(S, i - 1 + c, j + 1, -0.5, hi);
-        for (int s = 0; s < 2; ++s)
-          for (int q = 0; q < nc; ++q)
-            for (int n = 0; n <= ORD; ++n) line[c][s][q][n] = 0.5 * (lo[s][q][n] + hi[s][q][n]);
-      }
-      int fL = cell_flag(S, i, j) | cell_flag(S, i, j + 1);
-      int fR = cell_flag(S, i + 1, j) | cell_flag(S, i + 1, j + 1);
-      Deriv a[4], b[4], dL[4], dR[4];
-      second_pass(P, P.dx, line, fL, fR, a, b);
-      to_xy(nc, a, 1, dL); to_xy(nc, b, 1, dR);
-      double tc[4][5], We[4];
-      grp_point(P, 0, dL, dR, tc);
-      taylor_state(nc, tc, dt, We);
-      for (int q = 0; q < nc; ++q) WC[((size_t)(j + 1) * (nx + 1) + (i + 1)) * nc + q] = We[q];
-    }
-  // Step 5: Eq. (3.2) and Eq. (3.10).
+    for (int i = -1; i < nx; ++i) corner(S, i, j, dt, &WC[((size_t)(j + 1) * (nx + 1) + (i + 1)) * nc]);
   for (int j = 0; j < ny; ++j)
-    for (int i = 0; i < nx; ++i)
+    for (int i = 0; i < nx; ++i) {
+      double Fx[2][4], Wx[2][4], Gy[2][4], Wy[2][4], Wc[2][2][4], w[4], v[4], y[4], z[4];
+      for (int q = 0; q < nc; ++q) {
+        for (int s = 0; s < 2; ++s) {
+          size_t ox = ((size_t)j * (nx + 1) + (i + s)) * nc + q;
+          size_t oy = ((size_t)(j + s) * nx + i) * nc + q;
+          Fx[s][q] = FX[ox]; Wx[s][q] = WX[ox]; Gy[s][q] = GY[oy]; Wy[s][q] = WY[oy];
+          for (int r = 0; r < 2; ++r) Wc[r][s][q] = WC[((size_t)(j + r) * (nx + 1) + (i + s)) * nc + q];
+        }
+      }
+      update_cell(S, i, j, dt, Fx, Wx, Gy, Wy, Wc, w, v, y, z);
       for (int q = 0; q < nc; ++q) {
         size_t o = ((size_t)q * ny + j) * nx + i;
-        auto fx = [&](int ii) { return ((size_t)j * (nx + 1) + ii) * nc + q; };
-        auto gy = [&](int jj) { return ((size_t)jj * nx + i) * nc + q; };
-        auto wc = [&](int ii, int jj) { return WC[((size_t)jj * (nx + 1) + ii) * nc + q]; };
-        Wn[o] = S.f[0][o] - dt / P.dx * (FX[fx(i + 1)] - FX[fx(i)]) -
-                dt / P.dy * (GY[gy(j + 1)] - GY[gy(j)]);
-        Vn[o] = (WX[fx(i + 1)] - WX[fx(i)]) / P.dx;
-        Yn[o] = (WY[gy(j + 1)] - WY[gy(j)]) / P.dy;
-        Zn[o] = (wc(i + 1, j + 1) - wc(i, j + 1) - wc(i + 1, j) + wc(i, j)) / (P.dx * P.dy);
+        Wn[o] = w[q]; Vn[o] = v[q]; Yn[o] = y[q]; Zn[o] = z[q];
       }
+    }
+}
+
+// The same step for the cells of a window [i0, i0+w) x [j0, j0+h) of the mesh (faces and
+// corners inside the window computed once); outputs are [field][comp][h][w].
+void step2d_window(const State& S, double dt, int i0, int j0, int w, int h, double* out) {
+  const Problem& P = *S.P;
+  const int nc = ncomp(P);
+  std::vector<double> FX((size_t)(w + 1) * h * nc), WX((size_t)(w + 1) * h * nc);
+  std::vector<double> GY((size_t)w * (h + 1) * nc), WY((size_t)w * (h + 1) * nc);
+  std::vector<double> WC((size_t)(w + 1) * (h + 1) * nc);
+  for (int b = 0; b < h; ++b)
+    for (int a = 0; a <= w; ++a) {
+      size_t o = ((size_t)b * (w + 1) + a) * nc;
+      xface(S, i0 + a - 1, j0 + b, dt, &FX[o], &WX[o]);
+    }
+  for (int b = 0; b <= h; ++b)
+    for (int a = 0; a < w; ++a) {
+      size_t o = ((size_t)b * w + a) * nc;
+      yface(S, i0 + a, j0 + b - 1, dt, &GY[o], &WY[o]);
+    }
+  for (int b = 0; b <= h; ++b)
+    for (int a = 0; a <= w; ++a) corner(S, i0 + a - 1, j0 + b - 1, dt, &WC[((size_t)b * (w + 1) + a) * nc]);
+  const size_t plane = (size_t)nc * w * h;
+  for (int b = 0; b < h; ++b)
+    for (int a = 0; a < w; ++a) {
+      double Fx[2][4], Wx[2][4], Gy[2][4], Wy[2][4], Wc[2][2][4], r[4][4];
+      for (int q = 0; q < nc; ++q)
+        for (int s2 = 0; s2 < 2; ++s2) {
+          size_t ox = ((size_t)b * (w + 1) + (a + s2)) * nc + q;
+          size_t oy = ((size_t)(b + s2) * w + a) * nc + q;
+          Fx[s2][q] = FX[ox]; Wx[s2][q] = WX[ox]; Gy[s2][q] = GY[oy]; Wy[s2][q] = WY[oy];
+          for (int r2 = 0; r2 < 2; ++r2) Wc[r2][s2][q] = WC[((size_t)(b + r2) * (w + 1) + (a + s2)) * nc + q];
+        }
+      update_cell(S, i0 + a, j0 + b, dt, Fx, Wx, Gy, Wy, Wc, r[0], r[1], r[2], r[3]);
+      for (int f = 0; f < 4; ++f)
+        for (int q = 0; q < nc; ++q) out[f * plane + ((size_t)q * h + b) * w + a] = r[f][q];
+    }
+}
+
+// The same step for a list of cells only (each cell's own faces and corners): the updated
+// W, V, Y, Z of cell k go to out[k*4*nc + field*nc + q].
+void step2d_cells(const State& S, double dt, int ncells, const int32_t* ij, double* out) {
+  const Problem& P = *S.P;
+  const int nc = ncomp(P);
+  for (int k = 0; k < ncells; ++k) {
+    const int i = ij[2 * k], j = ij[2 * k + 1];
+    double Fx[2][4], Wx[2][4], Gy[2][4], Wy[2][4], Wc[2][2][4];
+    for (int s = 0; s < 2; ++s) {
+      xface(S, i - 1 + s, j, dt, Fx[s], Wx[s]);
+      yface(S, i, j - 1 + s, dt, Gy[s], Wy[s]);
+      for (int r = 0; r < 2; ++r) corner(S, i - 1 + s, j - 1 + r, dt, Wc[r][s]);
+    }
+    double* o = out + (size_t)k * 4 * nc;
+    update_cell(S, i, j, dt, Fx, Wx, Gy, Wy, Wc, o, o + nc, o + 2 * nc, o + 3 * nc);
+  }
 }
 
 // ----------------------------------------------------------------------------------------
@@ -875,7 +977,7 @@ void orc_upwind(const orc_problem* P, int dir, const double* Ws, const double* d
   double lam[4], R[16], L[16];
   eigensystem(*P, dir, Ws, lam, R);
   invert(ncomp(*P), R, L);
-  upwind(ncomp(*P), lam, R, L, dL, dR, out);
+  upwind(ncomp(*P), lam, wave_scale(*P, Ws, Ws[0], Ws[0]), R, L, dL, dR, out);
 }
 // CK on given spatial derivatives d[q][m][n] (= d^{m+n}W_q/dx^m dy^n, a 5x5 block per
 // component); returns all mixed derivatives out[q][m][n][k] = d^{m+n+k} W_q/dx^m dy^n dt^k.
@@ -917,6 +1019,22 @@ void orc_step(const orc_problem* P, const double* W, const double* V, const doub
   State S{P, {W, V, Y, Z}, flag, t};
   if (P->dim == 1) step1d(*P, S, dt, Wn, Vn);
   else step2d(*P, S, dt, Wn, Vn, Yn, Zn);
+}
+
+// One 2D step restricted to the listed cells (ij = i0, j0, i1, j1, ...); out[k][field][q].
+void orc_step2d_cells(const orc_problem* P, const double* W, const double* V, const double* Y,
+                      const double* Z, const uint8_t* flag, double t, double dt, int ncells,
+                      const int32_t* ij, double* out) {
+  State S{P, {W, V, Y, Z}, flag, t};
+  step2d_cells(S, dt, ncells, ij, out);
+}
+
+// One 2D step restricted to a window of cells; out[field][comp][h][w].
+void orc_step2d_window(const orc_problem* P, const double* W, const double* V, const double* Y,
+                       const double* Z, const uint8_t* flag, double t, double dt, int i0, int j0,
+                       int w, int h, double* out) {
+  State S{P, {W, V, Y, Z}, flag, t};
+  step2d_window(S, dt, i0, j0, w, h, out);
 }
 
 // Runs to t_final with dt = cfl / max_rate, the last step shortened to land on t_final.

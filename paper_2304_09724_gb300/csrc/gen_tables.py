@@ -1,0 +1,85 @@
+"""Writes recon_tables.cuh: exact rational constants of the SHWENO reconstruction used by the
+CUDA kernels (Section 2.4 reading: quartic p1 on {I_{j-1}, I_j, I_{j+1}} matching the three
+cell averages and the derivative averages of the two outer cells; linear p2, p3; Jiang-Shu
+smoothness indicators).  Run:  python gen_tables.py  (needs sympy; output is committed).
+
+In the local coordinate xi in [-1/2, 1/2] the data of cell j are W- = W_{j-1}, W0 = W_j,
+W+ = W_{j+1}, v- = h V_{j-1}, v+ = h V_{j+1}.  With the symmetric combinations
+  s = W- + W+, dv = v+ - v-   (even part of p1)   and   a = W+ - W-, sv = v- + v+   (odd part)
+the monomial coefficients of p1 split into c0, c2, c4 (from W0, s, dv) and c1, c3 (from a, sv).
+"""
+import os
+
+import sympy as sp
+
+xi = sp.Symbol("xi")
+half = sp.Rational(1, 2)
+
+
+def derive():
+    c = sp.symbols("c0:5")
+    Wm, W0, Wp, vm, vp = sp.symbols("Wm W0 Wp vm vp")
+    P = sum(c[k] * xi ** k for k in range(5))
+    eqs = [sp.integrate(P, (xi, l - half, l + half)) - w for l, w in ((-1, Wm), (0, W0), (1, Wp))]
+    eqs += [P.subs(xi, l + half) - P.subs(xi, l - half) - w for l, w in ((-1, vm), (1, vp))]
+    sol = sp.solve(eqs, c)
+    s, dv, a, sv = sp.symbols("s dv a sv")
+    # substitute W- = (s - a)/2, W+ = (s + a)/2, v- = (sv - dv)/2, v+ = (sv + dv)/2
+    sub = {Wm: (s - a) / 2, Wp: (s + a) / 2, vm: (sv - dv) / 2, vp: (sv + dv) / 2}
+    coef = {}
+    for k in range(5):
+        e = sp.expand(sol[c[k]].subs(sub))
+        coef[k] = {v: e.coeff(v) for v in (W0, s, dv, a, sv)}
+    # smoothness indicator of p1 as a quadratic form in c1..c4
+    cc = sp.symbols("k0:5")
+    Pc = sum(cc[k] * xi ** k for k in range(5))
+    beta = sp.expand(sum(sp.integrate(sp.diff(Pc, xi, d) ** 2, (xi, -half, half)) for d in range(1, 5)))
+    bq = {}
+    for i in range(1, 5):
+        for j in range(i, 5):
+            bq[(i, j)] = beta.coeff(cc[i], 1).coeff(cc[j], 1) if i != j else beta.coeff(cc[i], 2)
+    return coef, bq, (W0, s, dv, a, sv)
+
+
+def frac(r):
+    r = sp.Rational(r)
+    if r.q == 1:
+        return f"{float(r.p):.1f}"
+    return f"({float(r.p):.1f} / {float(r.q):.1f})"
+
+
+def main():
+    coef, bq, names = derive()
+    g = sp.sqrt(sp.Rational(15)) / 10  # Gauss node offset in [-1/2,1/2]
+    lines = [
+        "// Generated by gen_tables.py -- exact rational constants of the SHWENO reconstruction.",
+        "// Do not edit by hand.",
+        "#pragma once",
+        "namespace shweno_tables {",
+        "// p1 monomial coefficients: c_k = sum of COEF_k_<v> * v over v in {W0, s, dv, a, sv}.",
+    ]
+    for k in range(5):
+        for v in names:
+            lines.append(f"constexpr double P1_C{k}_{v} = {frac(coef[k][v])};")
+    lines.append("// smoothness indicator of p1: beta1 = sum_{i<=j} B_ij c_i c_j (i, j >= 1)")
+    for (i, j), val in bq.items():
+        lines.append(f"constexpr double BETA_{i}{j} = {frac(val)};")
+    lines.append("// 3-point Gauss nodes on [-1/2, 1/2] (offset) and weights")
+    lines.append("constexpr double GAUSS_G = 0.38729833462074168852;  // sqrt(15)/10")
+    lines.append("constexpr double GAUSS_W0 = (5.0 / 18.0), GAUSS_W1 = (8.0 / 18.0);")
+    lines.append("// 4-point Gauss-Lobatto nodes and weights on [0, 1]")
+    lines.append("constexpr double LOB_L1 = 0.27639320225002103036;  // 1/2 - sqrt(5)/10")
+    lines.append("constexpr double LOB_L2 = 0.72360679774997896964;  // 1/2 + sqrt(5)/10")
+    lines.append("constexpr double LOB_W0 = (1.0 / 12.0), LOB_W1 = (5.0 / 12.0);")
+    lines.append("}  // namespace shweno_tables")
+    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "recon_tables.cuh")
+    with open(out, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    # check the printed decimal constants against high-precision values
+    assert abs(float(g) - 0.38729833462074168852) < 1e-17
+    assert abs(float(half - sp.sqrt(5) / 10) - 0.27639320225002103036) < 1e-17
+    print("wrote", out)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,49 @@
+// Generated by gen_tables.py -- exact rational constants of the SHWENO reconstruction.
+// Do not edit by hand.
+#pragma once
+namespace shweno_tables {
+// p1 monomial coefficients: c_k = sum of COEF_k_<v> * v over v in {W0, s, dv, a, sv}.
+constexpr double P1_C0_W0 = (287.0 / 240.0);
+constexpr double P1_C0_s = (-47.0 / 480.0);
+constexpr double P1_C0_dv = (9.0 / 320.0);
+constexpr double P1_C0_a = 0.0;
+constexpr double P1_C0_sv = 0.0;
+constexpr double P1_C1_W0 = 0.0;
+constexpr double P1_C1_s = 0.0;
+constexpr double P1_C1_dv = 0.0;
+constexpr double P1_C1_a = (13.0 / 16.0);
+constexpr double P1_C1_sv = (-5.0 / 16.0);
+constexpr double P1_C2_W0 = (-5.0 / 2.0);
+constexpr double P1_C2_s = (5.0 / 4.0);
+constexpr double P1_C2_dv = (-3.0 / 8.0);
+constexpr double P1_C2_a = 0.0;
+constexpr double P1_C2_sv = 0.0;
+constexpr double P1_C3_W0 = 0.0;
+constexpr double P1_C3_s = 0.0;
+constexpr double P1_C3_dv = 0.0;
+constexpr double P1_C3_a = (-1.0 / 4.0);
+constexpr double P1_C3_sv = (1.0 / 4.0);
+constexpr double P1_C4_W0 = 1.0;
+constexpr double P1_C4_s = (-1.0 / 2.0);
+constexpr double P1_C4_dv = (1.0 / 4.0);
+constexpr double P1_C4_a = 0.0;
+constexpr double P1_C4_sv = 0.0;
+// smoothness indicator of p1: beta1 = sum_{i<=j} B_ij c_i c_j (i, j >= 1)
+constexpr double BETA_11 = 1.0;
+constexpr double BETA_12 = 0.0;
+constexpr double BETA_13 = (1.0 / 2.0);
+constexpr double BETA_14 = 0.0;
+constexpr double BETA_22 = (13.0 / 3.0);
+constexpr double BETA_23 = 0.0;
+constexpr double BETA_24 = (21.0 / 5.0);
+constexpr double BETA_33 = (3129.0 / 80.0);
+constexpr double BETA_34 = 0.0;
+constexpr double BETA_44 = (87617.0 / 140.0);
+// 3-point Gauss nodes on [-1/2, 1/2] (offset) and weights
+constexpr double GAUSS_G = 0.38729833462074168852;  // sqrt(15)/10
+constexpr double GAUSS_W0 = (5.0 / 18.0), GAUSS_W1 = (8.0 / 18.0);
+// 4-point Gauss-Lobatto nodes and weights on [0, 1]
+constexpr double LOB_L1 = 0.27639320225002103036;  // 1/2 - sqrt(5)/10
+constexpr double LOB_L2 = 0.72360679774997896964;  // 1/2 + sqrt(5)/10
+constexpr double LOB_W0 = (1.0 / 12.0), LOB_W1 = (5.0 / 12.0);
+}  // namespace shweno_tables

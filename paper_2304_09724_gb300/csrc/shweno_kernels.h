@@ -1,0 +1,37 @@
+// Host-side launchers of the step kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "shweno_device.cuh"
+
+namespace shweno {
+
+// Scratch buffers of one 2D step (all device memory owned by the handle).
+struct Scratch2D {
+  double* ycoef;  // [2 sets][4 comps][5 coefs][ny+2][nx+4]
+  double* xcoef;  // [2 sets][4 comps][5 coefs][nx][ny+4]
+  double* FX;     // [3 gauss][ncomp][ny][nx+1]  time-averaged x-flux per Gauss point
+  double* WX;     // [3 gauss][ncomp][ny][nx+1]  state at t_{n+1} per Gauss point
+  double* FY;     // [3 gauss][ncomp][ny+1][nx]
+  double* WY;     // [3 gauss][ncomp][ny+1][nx]
+  double* WC;     // [ncomp][ny+1][nx+1]          state at t_{n+1} at cell corners
+};
+
+// ev: NULL, or events recorded before each kernel and after the last (kernels + 1 events).
+constexpr int kKernels1D = 2;
+constexpr int kKernels2D = 4;
+void launch_step1d(const Params& P, Ctl* ctl, const double* s0, const double* s1, double* o0,
+                   double* o1, const uint8_t* flag, double* FH, double* WE, cudaStream_t st,
+                   cudaEvent_t* ev);
+void launch_step2d(const Params& P, Ctl* ctl, const double* s0, const double* s1, double* o0,
+                   double* o1, const uint8_t* flag, const Scratch2D& S, cudaStream_t st,
+                   cudaEvent_t* ev);
+size_t scratch2d_doubles(const Params& P);
+Scratch2D carve_scratch2d(const Params& P, double* base);
+void launch_begin_step(Ctl* ctl, cudaStream_t st);
+void launch_end_step(Ctl* ctl, cudaStream_t st);
+void launch_rate(const Params& P, Ctl* ctl, const double* s0, const double* s1, cudaStream_t st);
+
+}  // namespace shweno

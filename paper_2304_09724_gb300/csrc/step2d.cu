@@ -1,0 +1,425 @@
+// One ADER-SHWENO time step in two space dimensions (Section 3; Section 4 Steps 1-5).
+//
+// The SHWENO reconstruction runs dimension by dimension (Section 3.2): a first 1D pass along
+// the face gives line averages of W and of its normal derivative as polynomials in the
+// tangential coordinate, a second pass across the face gives all mixed derivatives
+// d^{m+n}W/dx^m dy^n (m + n <= 4) on both sides of each face quadrature point.
+//
+//   coef2d   one thread per cell (ghost ring included): the first-pass polynomials of both
+//            directions, y-pass on {W, Y} and {V, Z}, x-pass on {W, V} and {Y, Z}; the stencil
+//            tile (16 fields with a one-cell halo) is staged in shared memory.
+//   xface2d  one CTA per 128 x-faces of a row and one Gauss point (or the corner row): the CTA
+//            evaluates the y-pass polynomials of the 131 columns it needs at eta_g into shared
+//            memory, then each thread owns one face point: x-pass on both sides, HLLC leading
+//            term (Eq. 3.6), eigen-upwinded derivatives (Eq. 3.7), Cauchy-Kovalevskaya
+//            (Section 3.1), Lobatto flux (Eq. 3.8) and W(t_{n+1}) (Eq. 3.11).  The corner row
+//            averages the y-pass traces of the rows below and above and keeps only W(t_{n+1}).
+//   yface2d  the same for y-faces, one CTA per 128 faces of a column.
+//   update2d one thread per cell: Eq. (3.2) and Eq. (3.10), physical check, CFL rate.
+#include <cuda_runtime.h>
+
+#include "ck_generated.cuh"
+#include "shweno_device.cuh"
+#include "shweno_kernels.h"
+
+namespace shweno {
+
+constexpr int SEG = 128;       // face points per CTA
+constexpr int SPAN = SEG + 3;  // first-pass evaluations a CTA needs
+constexpr int TX = 32, TY = 8; // coef2d tile
+
+__device__ __forceinline__ void taylor_shift2(double e[5], double xi0, int mmax) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (i > mmax) break;
+#pragma unroll
+    for (int k = 3; k >= 0; --k)
+      if (k >= i) e[k] += xi0 * e[k + 1];
+  }
+}
+
+// ------------------------------------------------------------------ first pass
+__global__ void __launch_bounds__(TX * TY) coef2d_kernel(Params P, const Ctl* __restrict__ ctl,
+                                                         const double* s0, const double* s1,
+                                                         const uint8_t* __restrict__ flag,
+                                                         double* __restrict__ ycoef,
+                                                         double* __restrict__ xcoef) {
+  __shared__ double tile[16][TY + 2][TX + 2];
+  if (!ctl->active) return;
+  const double* st = (ctl->nsteps & 1) ? s1 : s0;
+  const double t = ctl->t;
+  const int bx = blockIdx.x * TX - 2, by = blockIdx.y * TY - 2;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  for (int idx = tid; idx < 16 * (TY + 2) * (TX + 2); idx += TX * TY) {
+    const int xx = idx % (TX + 2), rest = idx / (TX + 2);
+    const int yy = rest % (TY + 2), fq = rest / (TY + 2);
+    const int i = bx - 1 + xx, j = by - 1 + yy;
+    double v = 0.0;
+    if (i >= -3 && i <= P.nx + 2 && j >= -3 && j <= P.ny + 2) v = fetch(P, st, fq >> 2, fq & 3, i, j, t);
+    tile[fq][yy][xx] = v;
+  }
+  __syncthreads();
+  const int ic = bx + threadIdx.x, jr = by + threadIdx.y;
+  const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
+  const int NX4 = P.nx + 4, NY2 = P.ny + 2, NY4 = P.ny + 4;
+  if (ic <= P.nx + 1 && jr >= -1 && jr <= P.ny) {  // y-pass: {W,Y} and {V,Z} along a column
+    const int nl = cell_flag(P, flag, ic, jr);
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int fa = (s == 0 ? 0 : 1) * 4 + q, fd = (s == 0 ? 2 : 3) * 4 + q;
+        const double Wm = tile[fa][ly - 1][lx], W0 = tile[fa][ly][lx], Wp = tile[fa][ly + 1][lx];
+        const double vm = P.dy * tile[fd][ly - 1][lx], vp = P.dy * tile[fd][ly + 1][lx];
+        double c[5], C[5];
+        p1_coeffs(Wm, W0, Wp, vm, vp, c);
+        mix_coeffs(shweno_mix(P, Wm, W0, Wp, c, nl), Wm, W0, Wp, c, C);
+        const double sc = s == 0 ? 1.0 : P.dx;  // x-pass derivative data: dx * avg(W_x)
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+          ycoef[((size_t)((s * 4 + q) * 5 + k) * NY2 + (jr + 1)) * NX4 + (ic + 2)] = sc * C[k];
+      }
+  }
+  if (ic >= 0 && ic < P.nx && jr <= P.ny + 1) {  // x-pass: {W,V} and {Y,Z} along a row
+    const int nl = cell_flag(P, flag, ic, jr);
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int fa = (s == 0 ? 0 : 2) * 4 + q, fd = (s == 0 ? 1 : 3) * 4 + q;
+        const double Wm = tile[fa][ly][lx - 1], W0 = tile[fa][ly][lx], Wp = tile[fa][ly][lx + 1];
+        const double vm = P.dx * tile[fd][ly][lx - 1], vp = P.dx * tile[fd][ly][lx + 1];
+        double c[5], C[5];
+        p1_coeffs(Wm, W0, Wp, vm, vp, c);
+        mix_coeffs(shweno_mix(P, Wm, W0, Wp, c, nl), Wm, W0, Wp, c, C);
+        const double sc = s == 0 ? 1.0 : P.dy;  // y-pass derivative data: dy * avg(W_y)
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+          xcoef[((size_t)((s * 4 + q) * 5 + k) * P.nx + ic) * NY4 + (jr + 2)] = sc * C[k];
+      }
+  }
+}
+
+// ------------------------------------------------------------------ one face point
+// Second pass across the face for one side.  ev[set*4+q][k][col] holds the first-pass
+// Taylor coefficients (order k along the face) of the three stencil columns c0..c0+2; the
+// weights come from the order-0 data and serve every order (remark ending Section 2.1.2).
+struct SideMix { Mix m[4]; };
+
+__device__ __forceinline__ void side_weights(const Params& P, const double (*ev)[5][SPAN], int c0,
+                                             int nonlinear, SideMix& sm) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double Wm = ev[q][0][c0], W0 = ev[q][0][c0 + 1], Wp = ev[q][0][c0 + 2];
+    double c[5];
+    p1_coeffs(Wm, W0, Wp, ev[4 + q][0][c0], ev[4 + q][0][c0 + 2], c);
+    sm.m[q] = shweno_mix(P, Wm, W0, Wp, c, nonlinear);
+  }
+}
+
+// Cross-face Taylor coefficients e[p] (p <= 4 - k) of tangential order k, component q.
+__device__ __forceinline__ void side_column(const double (*ev)[5][SPAN], int c0, const Mix& mx,
+                                            int q, int k, double xi0, double e[5]) {
+  const double Wm = ev[q][k][c0], W0 = ev[q][k][c0 + 1], Wp = ev[q][k][c0 + 2];
+  double c[5];
+  p1_coeffs(Wm, W0, Wp, ev[4 + q][k][c0], ev[4 + q][k][c0 + 2], c);
+  mix_coeffs(mx, Wm, W0, Wp, c, e);
+  taylor_shift2(e, xi0, 4 - k);
+}
+
+// Face point: both sides' second pass, HLLC, upwinding, CK; returns the time-Taylor
+// coefficients tc[q][0..4].  dir = 0: x-face (first pass along y), 1: y-face.
+__device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5][SPAN], int c0,
+                                           int nlL, int nlR, int dir, double tc[4][5]) {
+  const double g = P.gamma;
+  SideMix L, R;
+  side_weights(P, ev, c0, nlL, L);
+  side_weights(P, ev, c0 + 1, nlR, R);
+  double a[4][25];
+  double dl[4][5], dr[4][5];
+  // tangential order 0 first: it carries the leading-term data
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    side_column(ev, c0, L.m[q], q, 0, 0.5, dl[q]);
+    side_column(ev, c0 + 1, R.m[q], q, 0, -0.5, dr[q]);
+  }
+  double WL[4], WR[4], Ws[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) { WL[q] = dl[q][0]; WR[q] = dr[q][0]; }
+  hllc_state<4>(WL, WR, g, dir, Ws);
+  Upwinder<4> U;
+  U.setup(Ws, g, dir);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    if (k > 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        side_column(ev, c0, L.m[q], q, k, 0.5, dl[q]);
+        side_column(ev, c0 + 1, R.m[q], q, k, -0.5, dr[q]);
+      }
+    }
+#pragma unroll
+    for (int p = 0; p + k <= 4; ++p) {
+      if (p == 0 && k == 0) continue;
+      double x[4], y[4], o[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { x[q] = dl[q][p]; y[q] = dr[q][p]; }
+      U.apply(x, y, o);
+      // p is the order across the face, k the order along it
+      const int idx = dir == 0 ? p * 5 + k : k * 5 + p;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a[q][idx] = o[q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) a[q][0] = Ws[q];
+  double cx[5][4], cy[5][4];
+  const double ihx = 1.0 / P.dx, ihy = 1.0 / P.dy;
+#pragma unroll
+  for (int m = 0; m < 5; ++m)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      cx[m][k] = (m + 1) * ihx / (k + 1);
+      cy[m][k] = (m + 1) * ihy / (k + 1);
+    }
+  double t4[4][5];
+  ck_euler2d(a, t4, cx, cy, g - 1.0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    tc[q][0] = Ws[q];
+#pragma unroll
+    for (int k = 1; k < 5; ++k) tc[q][k] = t4[q][k];
+  }
+}
+
+// Lobatto time average of the flux along dir and the state at tau = dt.
+__device__ __forceinline__ void lobatto(const double tc[4][5], double dt, double g, int dir,
+                                        double Fh[4], double We[4]) {
+  using namespace shweno_tables;
+  const double taus[4] = {0.0, LOB_L1 * dt, LOB_L2 * dt, dt};
+  const double wts[4] = {LOB_W0, LOB_W1, LOB_W1, LOB_W0};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) Fh[q] = 0.0;
+#pragma unroll
+  for (int al = 0; al < 4; ++al) {
+    double W[4], F[4];
+    const double tau = taus[al];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      W[q] = (((tc[q][4] * tau + tc[q][3]) * tau + tc[q][2]) * tau + tc[q][1]) * tau + tc[q][0];
+    phys_flux<4>(W, g, dir, F);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Fh[q] += wts[al] * F[q];
+    if (al == 3) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) We[q] = W[q];
+    }
+  }
+}
+
+__device__ __forceinline__ double state_at(const double tc[5], double tau) {
+  return (((tc[4] * tau + tc[3]) * tau + tc[2]) * tau + tc[1]) * tau + tc[0];
+}
+
+// ------------------------------------------------------------------ x-faces and corners
+__global__ void __launch_bounds__(SEG) xface2d_kernel(Params P, const Ctl* __restrict__ ctl,
+                                                      const double* __restrict__ ycoef,
+                                                      const uint8_t* __restrict__ flag,
+                                                      double* __restrict__ FX,
+                                                      double* __restrict__ WX,
+                                                      double* __restrict__ WC) {
+  __shared__ double ev[8][5][SPAN];
+  if (!ctl->active) return;
+  const int slice = blockIdx.z;  // 0..2: Gauss point of the rows; 3: corner rows
+  const int row = blockIdx.y;    // Gauss: cell row j; corner: corner row jc (y_{jc-1/2})
+  if (slice < 3 && row >= P.ny) return;
+  const int f0 = blockIdx.x * SEG;
+  const int NX4 = P.nx + 4, NY2 = P.ny + 2;
+  using namespace shweno_tables;
+  for (int it = threadIdx.x; it < 8 * SPAN; it += SEG) {
+    const int col = it % SPAN, rq = it / SPAN;
+    const int tcol = f0 + col;
+    if (tcol >= NX4) continue;
+    double e[5];
+    if (slice < 3) {
+      const double* src = ycoef + ((size_t)(rq * 5) * NY2 + (row + 1)) * NX4 + tcol;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) e[k] = src[(size_t)k * NY2 * NX4];
+      if (slice != 1) taylor_shift2(e, slice == 0 ? -GAUSS_G : GAUSS_G, 4);
+    } else {
+      double lo[5], hi[5];
+      const double* slo = ycoef + ((size_t)(rq * 5) * NY2 + row) * NX4 + tcol;
+      const double* shi = slo + NX4;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) { lo[k] = slo[(size_t)k * NY2 * NX4]; hi[k] = shi[(size_t)k * NY2 * NX4]; }
+      taylor_shift2(lo, 0.5, 4);
+      taylor_shift2(hi, -0.5, 4);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) e[k] = 0.5 * (lo[k] + hi[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) ev[rq][k][col] = e[k];
+  }
+  __syncthreads();
+  const int fi = f0 + threadIdx.x;  // face x_{fi-1/2}
+  if (fi > P.nx) return;
+  int nlL, nlR;
+  if (slice < 3) {
+    nlL = cell_flag(P, flag, fi - 1, row);
+    nlR = cell_flag(P, flag, fi, row);
+  } else {
+    nlL = cell_flag(P, flag, fi - 1, row - 1) | cell_flag(P, flag, fi - 1, row);
+    nlR = cell_flag(P, flag, fi, row - 1) | cell_flag(P, flag, fi, row);
+  }
+  double tc[4][5];
+  face_point(P, ev, threadIdx.x, nlL, nlR, 0, tc);
+  const double dt = ctl->dt;
+  if (slice < 3) {
+    double Fh[4], We[4];
+    lobatto(tc, dt, P.gamma, 0, Fh, We);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const size_t o = ((size_t)(slice * 4 + q) * P.ny + row) * (P.nx + 1) + fi;
+      FX[o] = Fh[q];
+      WX[o] = We[q];
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) WC[((size_t)q * (P.ny + 1) + row) * (P.nx + 1) + fi] = state_at(tc[q], dt);
+  }
+}
+
+// ------------------------------------------------------------------ y-faces
+__global__ void __launch_bounds__(SEG) yface2d_kernel(Params P, const Ctl* __restrict__ ctl,
+                                                      const double* __restrict__ xcoef,
+                                                      const uint8_t* __restrict__ flag,
+                                                      double* __restrict__ FY,
+                                                      double* __restrict__ WY) {
+  __shared__ double ev[8][5][SPAN];
+  if (!ctl->active) return;
+  const int slice = blockIdx.z;  // Gauss point of the columns
+  const int col = blockIdx.y;    // cell column i
+  const int f0 = blockIdx.x * SEG;
+  const int NY4 = P.ny + 4;
+  using namespace shweno_tables;
+  for (int it = threadIdx.x; it < 8 * SPAN; it += SEG) {
+    const int r = it % SPAN, rq = it / SPAN;
+    const int trow = f0 + r;
+    if (trow >= NY4) continue;
+    double e[5];
+    const double* src = xcoef + ((size_t)(rq * 5) * P.nx + col) * NY4 + trow;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) e[k] = src[(size_t)k * P.nx * NY4];
+    if (slice != 1) taylor_shift2(e, slice == 0 ? -GAUSS_G : GAUSS_G, 4);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) ev[rq][k][r] = e[k];
+  }
+  __syncthreads();
+  const int fj = f0 + threadIdx.x;  // face y_{fj-1/2}
+  if (fj > P.ny) return;
+  const int nlB = cell_flag(P, flag, col, fj - 1);
+  const int nlT = cell_flag(P, flag, col, fj);
+  double tc[4][5];
+  face_point(P, ev, threadIdx.x, nlB, nlT, 1, tc);
+  double Gh[4], We[4];
+  lobatto(tc, ctl->dt, P.gamma, 1, Gh, We);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const size_t o = ((size_t)(slice * 4 + q) * (P.ny + 1) + fj) * P.nx + col;
+    FY[o] = Gh[q];
+    WY[o] = We[q];
+  }
+}
+
+// ------------------------------------------------------------------ update
+__global__ void __launch_bounds__(256) update2d_kernel(Params P, Ctl* __restrict__ ctl,
+                                                       const double* s0, const double* s1,
+                                                       double* o0, double* o1,
+                                                       const double* __restrict__ FX,
+                                                       const double* __restrict__ WX,
+                                                       const double* __restrict__ FY,
+                                                       const double* __restrict__ WY,
+                                                       const double* __restrict__ WC) {
+  __shared__ double red[32];
+  if (!ctl->active) return;
+  const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
+  const bool odd = ctl->nsteps & 1;
+  const double* st = odd ? s1 : s0;
+  double* out = odd ? o0 : o1;
+  const double dt = ctl->dt;
+  const int nx = P.nx, ny = P.ny;
+  using namespace shweno_tables;
+  const double gw[3] = {GAUSS_W0, GAUSS_W1, GAUSS_W0};
+  double rate = 0.0;
+  if (i < nx && j < ny) {
+    double Wn[4];
+    const size_t cells = (size_t)nx * ny, c = (size_t)j * nx + i;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double fl = 0.0, fr = 0.0, gb = 0.0, gt = 0.0, wl = 0.0, wr = 0.0, wb = 0.0, wt = 0.0;
+#pragma unroll
+      for (int g = 0; g < 3; ++g) {
+        const size_t ox = ((size_t)(g * 4 + q) * ny + j) * (nx + 1) + i;
+        const size_t oy = ((size_t)(g * 4 + q) * (ny + 1) + j) * nx + i;
+        fl += gw[g] * FX[ox];
+        fr += gw[g] * FX[ox + 1];
+        wl += gw[g] * WX[ox];
+        wr += gw[g] * WX[ox + 1];
+        gb += gw[g] * FY[oy];
+        gt += gw[g] * FY[oy + nx];
+        wb += gw[g] * WY[oy];
+        wt += gw[g] * WY[oy + nx];
+      }
+      const size_t oc = ((size_t)q * (ny + 1) + j) * (nx + 1) + i;
+      const double z = (WC[oc + (nx + 1) + 1] - WC[oc + (nx + 1)] - WC[oc + 1] + WC[oc]) / (P.dx * P.dy);
+      Wn[q] = st[q * cells + c] - dt / P.dx * (fr - fl) - dt / P.dy * (gt - gb);
+      out[q * cells + c] = Wn[q];
+      out[(4 + q) * cells + c] = (wr - wl) / P.dx;
+      out[(8 + q) * cells + c] = (wt - wb) / P.dy;
+      out[(12 + q) * cells + c] = z;
+    }
+    if (!cell_physical(P, Wn)) atomicCAS(&ctl->err, ERR_NONE, ERR_NONPHYSICAL);
+    else rate = cell_rate(P, Wn);
+  }
+  block_max_rate(rate, &ctl->rate_next, red);
+}
+
+// ------------------------------------------------------------------ host side
+size_t scratch2d_doubles(const Params& P) {
+  const size_t nx = P.nx, ny = P.ny;
+  return 40 * (ny + 2) * (nx + 4) + 40 * nx * (ny + 4) + 2 * 12 * ny * (nx + 1) +
+         2 * 12 * (ny + 1) * nx + 4 * (ny + 1) * (nx + 1);
+}
+
+Scratch2D carve_scratch2d(const Params& P, double* base) {
+  const size_t nx = P.nx, ny = P.ny;
+  Scratch2D S;
+  S.ycoef = base; base += 40 * (ny + 2) * (nx + 4);
+  S.xcoef = base; base += 40 * nx * (ny + 4);
+  S.FX = base; base += 12 * ny * (nx + 1);
+  S.WX = base; base += 12 * ny * (nx + 1);
+  S.FY = base; base += 12 * (ny + 1) * nx;
+  S.WY = base; base += 12 * (ny + 1) * nx;
+  S.WC = base;
+  return S;
+}
+
+void launch_step2d(const Params& P, Ctl* ctl, const double* s0, const double* s1, double* o0,
+                   double* o1, const uint8_t* flag, const Scratch2D& S, cudaStream_t st,
+                   cudaEvent_t* ev) {
+  dim3 cb(TX, TY), cg((P.nx + 4 + TX - 1) / TX, (P.ny + 4 + TY - 1) / TY);
+  if (ev) cudaEventRecord(ev[0], st);
+  coef2d_kernel<<<cg, cb, 0, st>>>(P, ctl, s0, s1, flag, S.ycoef, S.xcoef);
+  if (ev) cudaEventRecord(ev[1], st);
+  dim3 xg((P.nx + 1 + SEG - 1) / SEG, P.ny + 1, 4);
+  xface2d_kernel<<<xg, SEG, 0, st>>>(P, ctl, S.ycoef, flag, S.FX, S.WX, S.WC);
+  if (ev) cudaEventRecord(ev[2], st);
+  dim3 yg((P.ny + 1 + SEG - 1) / SEG, P.nx, 3);
+  yface2d_kernel<<<yg, SEG, 0, st>>>(P, ctl, S.xcoef, flag, S.FY, S.WY);
+  if (ev) cudaEventRecord(ev[3], st);
+  dim3 ug((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
+  update2d_kernel<<<ug, cb, 0, st>>>(P, ctl, s0, s1, o0, o1, S.FX, S.WX, S.FY, S.WY, S.WC);
+  if (ev) cudaEventRecord(ev[4], st);
+}
+
+}  // namespace shweno

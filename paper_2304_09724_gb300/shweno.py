@@ -1,0 +1,264 @@
+"""Thin ctypes binding of libshweno.so (include/shweno.h): the same entry points under the same
+names, with argument marshalling only.  Every step of the method runs in the library's CUDA
+kernels; nothing here computes.  Importing succeeds without the library, but every call raises
+if libshweno.so is missing or cannot be loaded: there is no fallback.
+
+Device memory and streams come from PyTorch when the caller uses torch tensors: a CUDA tensor
+is passed by its data_ptr() with on_device=1, and a torch stream by its cuda_stream handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libshweno.so")
+
+OK, E_INVALID, E_CUDA, E_NOMEM, E_NONPHYSICAL, E_TIMEOUT, E_STATE = range(7)
+BURGERS, EULER = 0, 1
+BC_PERIODIC, BC_OUTFLOW, BC_REFLECTIVE, BC_INFLOW, BC_DMR_BOTTOM, BC_DMR_TOP = range(6)
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "CUDA", 3: "NOMEM", 4: "NONPHYSICAL", 5: "TIMEOUT", 6: "STATE"}
+
+
+class shweno_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("eq", ctypes.c_int32), ("nx", ctypes.c_int64),
+                ("ny", ctypes.c_int64), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double)]
+
+
+class shweno_bc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32 * 4), ("inflow", (ctypes.c_double * 4) * 4)]
+
+
+class shweno_opts(ctypes.Structure):
+    _fields_ = [("flag_mode", ctypes.c_int32), ("eps", ctypes.c_double), ("gam", ctypes.c_double * 3)]
+
+
+class ShwenoError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"shweno {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+EXPORTS = ["shweno_create", "shweno_set_state", "shweno_get_state", "shweno_step", "shweno_run",
+           "shweno_advance", "shweno_sync", "shweno_set_timing", "shweno_get_timing",
+           "shweno_kernel_name", "shweno_cfl_dt", "shweno_get_time", "shweno_set_flags",
+           "shweno_destroy", "shweno_last_error", "shweno_set_allocator"]
+
+_lib = None
+
+
+def lib():
+    """Loads libshweno.so (raises if it is missing: the library has no CPU path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libshweno.so not built ({LIB_PATH}); run paper_2304_09724_gb300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)
+    st = ctypes.c_int
+    L.shweno_create.argtypes = [ctypes.POINTER(shweno_grid), ctypes.c_double, ctypes.POINTER(shweno_bc),
+                                ctypes.POINTER(shweno_opts), vp, ctypes.POINTER(vp)]
+    L.shweno_set_state.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_int]
+    L.shweno_get_state.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int]
+    L.shweno_step.argtypes = [vp, ctypes.c_double]
+    L.shweno_run.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, i64p]
+    L.shweno_cfl_dt.argtypes = [vp, ctypes.c_double, dp, dp]
+    L.shweno_get_time.argtypes = [vp, dp, i64p]
+    L.shweno_set_flags.argtypes = [vp, vp, ctypes.c_int]
+    L.shweno_destroy.argtypes = [vp]
+    L.shweno_advance.argtypes = [vp, ctypes.c_int64, ctypes.c_double]
+    L.shweno_sync.argtypes = [vp]
+    L.shweno_set_timing.argtypes = [vp, ctypes.c_int]
+    L.shweno_get_timing.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), i64p]
+    L.shweno_kernel_name.argtypes = [vp, ctypes.c_int]
+    L.shweno_kernel_name.restype = ctypes.c_char_p
+    L.shweno_set_allocator.argtypes = [vp, vp, vp]
+    L.shweno_last_error.argtypes = [vp]
+    L.shweno_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("shweno_last_error", "shweno_kernel_name"):
+            getattr(L, name).restype = st
+    _lib = L
+    return L
+
+
+def _check(status, h=None):
+    if status != OK:
+        msg = lib().shweno_last_error(h).decode()
+        raise ShwenoError(status, msg)
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or a torch tensor (float64 or uint8, contiguous)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    # torch tensor
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return a.data_ptr(), 1 if a.is_cuda else 0
+
+
+# --------------------------------------------------------------------------- C names
+def shweno_create(grid: shweno_grid, gamma: float, bc: shweno_bc, opts: shweno_opts | None = None,
+                  stream: int = 0):
+    h = ctypes.c_void_p()
+    s = lib().shweno_create(ctypes.byref(grid), gamma, ctypes.byref(bc),
+                            ctypes.byref(opts) if opts is not None else None, stream or None, ctypes.byref(h))
+    _check(s, None)
+    return h
+
+
+def shweno_set_state(h, W, V, Y=None, Z=None, t=0.0):
+    ptrs = [_ptr(a) for a in (W, V, Y, Z)]
+    dev = ptrs[0][1]
+    _check(lib().shweno_set_state(h, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], t, dev), h)
+
+
+def shweno_get_state(h, W, V, Y=None, Z=None):
+    ptrs = [_ptr(a) for a in (W, V, Y, Z)]
+    _check(lib().shweno_get_state(h, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], ptrs[0][1]), h)
+
+
+def shweno_step(h, dt):
+    _check(lib().shweno_step(h, dt), h)
+
+
+def shweno_run(h, t_final, cfl):
+    t = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(lib().shweno_run(h, t_final, cfl, ctypes.byref(t), ctypes.byref(n)), h)
+    return t.value, n.value
+
+
+def shweno_cfl_dt(h, cfl):
+    dt, rate = ctypes.c_double(), ctypes.c_double()
+    _check(lib().shweno_cfl_dt(h, cfl, ctypes.byref(dt), ctypes.byref(rate)), h)
+    return dt.value, rate.value
+
+
+def shweno_get_time(h):
+    t, n = ctypes.c_double(), ctypes.c_int64()
+    _check(lib().shweno_get_time(h, ctypes.byref(t), ctypes.byref(n)), h)
+    return t.value, n.value
+
+
+def shweno_set_flags(h, flags):
+    p, dev = _ptr(flags)
+    _check(lib().shweno_set_flags(h, p, dev), h)
+
+
+def shweno_advance(h, nsteps, cfl):
+    _check(lib().shweno_advance(h, nsteps, cfl), h)
+
+
+def shweno_sync(h):
+    _check(lib().shweno_sync(h), h)
+
+
+def shweno_set_timing(h, enable):
+    _check(lib().shweno_set_timing(h, 1 if enable else 0), h)
+
+
+def shweno_get_timing(h, max_kernels=8):
+    """Returns ({kernel name: total ms}, timed steps) and clears the totals."""
+    ms = (ctypes.c_double * max_kernels)()
+    nk, ns = ctypes.c_int(), ctypes.c_int64()
+    _check(lib().shweno_get_timing(h, ms, max_kernels, ctypes.byref(nk), ctypes.byref(ns)), h)
+    names = [lib().shweno_kernel_name(h, k).decode() for k in range(nk.value)]
+    return {n: ms[k] for k, n in enumerate(names)}, ns.value
+
+
+def shweno_destroy(h):
+    if h:
+        lib().shweno_destroy(h)
+
+
+def shweno_last_error(h=None):
+    return lib().shweno_last_error(h).decode()
+
+
+# --------------------------------------------------------------------------- convenience
+def make_grid(dim, eq, nx, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0):
+    g = shweno_grid()
+    g.dim, g.eq, g.nx, g.ny, g.x0, g.x1, g.y0, g.y1 = dim, eq, nx, ny, x0, x1, y0, y1
+    return g
+
+
+def make_bc(kinds, inflow=None):
+    b = shweno_bc()
+    for k in range(4):
+        b.kind[k] = kinds[k] if k < len(kinds) else 0
+    if inflow is not None:
+        for s in range(4):
+            for q in range(4):
+                b.inflow[s][q] = inflow[s][q]
+    return b
+
+
+def make_opts(flag_mode=0, eps=1e-6, gam=(0.994, 0.003, 0.003)):
+    o = shweno_opts()
+    o.flag_mode, o.eps = flag_mode, eps
+    for k in range(3):
+        o.gam[k] = gam[k]
+    return o
+
+
+class Solver:
+    """Owns one handle.  Arrays are float64 [ncomp][nx] (1D) or [ncomp][ny][nx] (2D), numpy (host)
+    or torch CUDA tensors (device)."""
+
+    def __init__(self, dim, eq, nx, ny=1, domain=(0.0, 1.0, 0.0, 1.0), bc=(0, 0, 0, 0), gamma=1.4,
+                 inflow=None, flag_mode=0, eps=1e-6, stream=0):
+        self.dim, self.eq, self.nx, self.ny = dim, eq, nx, (ny if dim == 2 else 1)
+        self.ncomp = 1 if eq == BURGERS else (3 if dim == 1 else 4)
+        self.h = shweno_create(make_grid(dim, eq, nx, ny, *domain), gamma, make_bc(bc, inflow),
+                               make_opts(flag_mode, eps), stream)
+
+    @property
+    def shape(self):
+        return (self.ncomp, self.nx) if self.dim == 1 else (self.ncomp, self.ny, self.nx)
+
+    def set_state(self, st, t=0.0):
+        f = lambda k: np.ascontiguousarray(st[k], dtype=np.float64) if isinstance(st[k], np.ndarray) else st[k]
+        if self.dim == 1:
+            shweno_set_state(self.h, f("W"), f("V"), None, None, t)
+        else:
+            shweno_set_state(self.h, f("W"), f("V"), f("Y"), f("Z"), t)
+
+    def get_state(self):
+        out = {k: np.empty(self.shape) for k in (("W", "V") if self.dim == 1 else ("W", "V", "Y", "Z"))}
+        shweno_get_state(self.h, out["W"], out["V"], out.get("Y"), out.get("Z"))
+        return out
+
+    def step(self, dt):
+        shweno_step(self.h, dt)
+
+    def run(self, t_final, cfl):
+        return shweno_run(self.h, t_final, cfl)
+
+    def set_flags(self, flags):
+        if isinstance(flags, np.ndarray):
+            flags = np.ascontiguousarray(flags, dtype=np.uint8)
+        shweno_set_flags(self.h, flags)
+
+    def time(self):
+        return shweno_get_time(self.h)
+
+    def close(self):
+        if self.h:
+            shweno_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

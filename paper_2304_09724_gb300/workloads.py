@@ -75,9 +75,9 @@ def project_2d(fun, x0, x1, y0, y1, nx, ny, nq=6, eps_edge=0.0):
     for V and Y, corners for Z).  eps_edge > 0 takes edge values just inside the cell, which is
     the limit from inside for piecewise-constant data."""
     dx, dy = (x1 - x0) / nx, (y1 - y0) / ny
-    xc = x0 + (np.arange(nx) + 0.5) * dx
-    yc = y0 + (np.arange(ny) + 0.5) * dy
-    X, Yg = np.meshgrid(xc, yc)  # [ny, nx]
+    # broadcastable coordinates ([1, nx] and [ny, 1]): separable functions stay cheap
+    X = (x0 + (np.arange(nx) + 0.5) * dx)[None, :]
+    Yg = (y0 + (np.arange(ny) + 0.5) * dy)[:, None]
     s, w = _gauss(nq)
     W = 0.0
     for sa, wa in zip(s, w):
@@ -93,7 +93,8 @@ def project_2d(fun, x0, x1, y0, y1, nx, ny, nq=6, eps_edge=0.0):
     Y = Y / dy
     Z = (fun(X + 0.5 * dx - ex, Yg + 0.5 * dy - ey) - fun(X - 0.5 * dx + ex, Yg + 0.5 * dy - ey)
          - fun(X + 0.5 * dx - ex, Yg - 0.5 * dy + ey) + fun(X - 0.5 * dx + ex, Yg - 0.5 * dy + ey)) / (dx * dy)
-    c = np.ascontiguousarray
+    full = (np.shape(W)[0], ny, nx)
+    c = lambda a: np.ascontiguousarray(np.broadcast_to(a, full))
     return c(W), c(V), c(Y), c(Z)
 
 
@@ -154,12 +155,17 @@ def vortex_fun(t=0.0, L=10.0, strength=5.0, gamma=GAMMA):
         cy = (5.0 + t) % L
         xr = (x - cx + 0.5 * L) % L - 0.5 * L
         yr = (y - cy + 0.5 * L) % L - 0.5 * L
-        r2 = xr * xr + yr * yr
-        e = np.exp(0.5 * (1.0 - r2))
-        rho = (1.0 - (gamma - 1.0) * strength ** 2 / (8.0 * gamma * math.pi ** 2) * e * e) ** (1.0 / (gamma - 1.0))
+        # exp((1 - r^2)/2) = e^(1/2) exp(-xr^2/2) exp(-yr^2/2): one exp per coordinate
+        e = math.exp(0.5) * np.exp(-0.5 * xr * xr) * np.exp(-0.5 * yr * yr)
+        base = 1.0 - (gamma - 1.0) * strength ** 2 / (8.0 * gamma * math.pi ** 2) * e * e
+        if gamma == 1.4:  # rho = base^2.5, p = rho^1.4 = base^3.5, without pow
+            rho = base * base * np.sqrt(base)
+            p = rho * base
+        else:
+            rho = base ** (1.0 / (gamma - 1.0))
+            p = rho ** gamma
         u = 1.0 - strength / (2.0 * math.pi) * e * yr
         v = 1.0 + strength / (2.0 * math.pi) * e * xr
-        p = rho ** gamma
         return euler_conserved(rho, u, p, v, gamma)
     return f
 
@@ -216,7 +222,7 @@ def quadrant_fun(states, xs=0.5, ys=0.5):
 
     def f(x, y):
         east, north = x >= xs, y >= ys
-        out = np.empty((4,) + np.shape(x))
+        out = np.empty((4,) + np.broadcast_shapes(np.shape(x), np.shape(y)))
         for q in range(4):
             out[q] = np.where(north, np.where(east, S[0][q], S[1][q]), np.where(east, S[3][q], S[2][q]))
         return out

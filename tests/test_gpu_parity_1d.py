@@ -1,0 +1,73 @@
+"""GPU parity, one space dimension: the CUDA step through the C ABI against the oracle."""
+import numpy as np
+import pytest
+
+from paper_2304_09724_gb300 import workloads as WL
+from tests import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+def test_burgers_example_5_1_full_run_n200():
+    """The small configuration: Burgers, N = 200, CFL 0.6, T = 0.5/pi, device-side time loop."""
+    wl = WL.burgers_sine(200)
+    g, o, (t, n), (t_o, n_o) = U.run_both(wl, wl.t_final)
+    assert n == n_o and t == t_o == wl.t_final
+    U.check(g, o, U.fields(wl), shocked=False, what="burgers N=200")
+
+
+@pytest.mark.parametrize("n", [4, 5, 17, 64, 129, 300])
+def test_burgers_sizes_fixed_steps(n):
+    """Sizes below, at and across the 128-face CTA width, with ragged tails."""
+    W, V = WL.random_smooth_1d(n, n, eq=WL.BURGERS)
+    wl = WL.burgers_sine(n)
+    wl.domain = (0.0, 1.0, 0.0, 1.0)
+    wl.state = {"W": W, "V": V}
+    g, o = U.steps_both(wl, [0.2 / n] * 3)
+    U.check(g, o, U.fields(wl), shocked=False, what=f"burgers n={n}")
+
+
+@pytest.mark.parametrize("n", [16, 130])
+@pytest.mark.parametrize("bc", [(WL.PERIODIC, WL.PERIODIC), (WL.OUTFLOW, WL.REFLECTIVE), (WL.REFLECTIVE, WL.INFLOW)])
+def test_euler1d_smooth_all_bcs(n, bc):
+    W, V = WL.random_smooth_1d(7, n)
+    wl = WL.euler1d_sine(n)
+    wl.domain = (0.0, 1.0, 0.0, 1.0)
+    wl.bc = bc + (0, 0)
+    wl.inflow = [list(W[:, -1]) + [0.0]] * 4
+    wl.state = {"W": W, "V": V}
+    g, o = U.steps_both(wl, [0.1 / n] * 4)
+    U.check(g, o, U.fields(wl), shocked=False, what=f"euler1d n={n} bc={bc}")
+
+
+def test_euler1d_example_5_2_run():
+    wl = WL.euler1d_sine(40)
+    g, o, (t, n), (t_o, n_o) = U.run_both(wl, 1.0)
+    assert n == n_o and t == t_o == 1.0
+    U.check(g, o, U.fields(wl), shocked=False, what="euler1d sine")
+
+
+@pytest.mark.parametrize("maker", [lambda: WL.sod(100), lambda: WL.lax(200), lambda: WL.random_riemann1d(3, nx=257)])
+def test_euler1d_shocked_runs(maker):
+    wl = maker()
+    T = min(wl.t_final, 0.05 if wl.name.startswith("riemann") else wl.t_final)
+    g, o, (t, n), (t_o, n_o) = U.run_both(wl, T)
+    assert n == n_o
+    U.check(g, o, U.fields(wl), shocked=True, what=wl.name)
+
+
+def test_linear_weights_mode():
+    W, V = WL.random_smooth_1d(11, 50)
+    wl = WL.euler1d_sine(50)
+    wl.domain = (0.0, 1.0, 0.0, 1.0)
+    wl.state = {"W": W, "V": V}
+    g, o = U.steps_both(wl, [0.002] * 3, flag_mode=1, linear=True)
+    U.check(g, o, U.fields(wl), shocked=False, what="linear weights")
+
+
+def test_per_cell_flags():
+    wl = WL.sod(64)
+    rng = np.random.default_rng(1)
+    flag = (rng.random(64) < 0.5).astype(np.uint8)
+    g, o = U.steps_both(wl, [0.004] * 3, flag=flag, flag_mode=2)
+    U.check(g, o, U.fields(wl), shocked=True, what="per-cell flags")

@@ -203,3 +203,18 @@ def test_dmr_small_runs_and_stays_physical():
     st, n, t = O.run(P, wl.state, 0.002, 0.6)
     rho = st["W"][0]
     assert np.isfinite(st["W"]).all() and rho.min() > 0
+
+
+def test_sampled_cell_step_equals_full_step():
+    """The per-cell entry used for parity on full-size meshes is the same computation."""
+    wl = WL.riemann2d(12, WL.LAX_LIU_SHOCKS)
+    P = problem_of(wl)
+    full = O.step(P, wl.state, 0.01)
+    cells = [(0, 0), (11, 11), (5, 6), (0, 7), (11, 3)]
+    part = O.step2d_cells(P, wl.state, 0.01, cells)
+    for k in "WVYZ":
+        for n, (i, j) in enumerate(cells):
+            assert np.array_equal(part[k][n], full[k][:, j, i])
+    win = O.step2d_window(P, wl.state, 0.01, 3, 2, 5, 7)
+    for k in "WVYZ":
+        assert np.array_equal(win[k], full[k][:, 2:9, 3:8])
