@@ -13,7 +13,7 @@ def test_burgers_example_5_1_full_run_n200():
     wl = WL.burgers_sine(200)
     g, o, (t, n), (t_o, n_o) = U.run_both(wl, wl.t_final)
     assert n == n_o and t == t_o == wl.t_final
-    U.check(g, o, U.fields(wl), shocked=False, what="burgers N=200")
+    U.check(g, o, U.fields(wl), shocked=False, what="burgers N=200", wl=wl)
 
 
 @pytest.mark.parametrize("n", [4, 5, 17, 64, 129, 300])
@@ -24,7 +24,7 @@ def test_burgers_sizes_fixed_steps(n):
     wl.domain = (0.0, 1.0, 0.0, 1.0)
     wl.state = {"W": W, "V": V}
     g, o = U.steps_both(wl, [0.2 / n] * 3)
-    U.check(g, o, U.fields(wl), shocked=False, what=f"burgers n={n}")
+    U.check(g, o, U.fields(wl), shocked=False, what=f"burgers n={n}", wl=wl)
 
 
 @pytest.mark.parametrize("n", [16, 130])
@@ -37,14 +37,14 @@ def test_euler1d_smooth_all_bcs(n, bc):
     wl.inflow = [list(W[:, -1]) + [0.0]] * 4
     wl.state = {"W": W, "V": V}
     g, o = U.steps_both(wl, [0.1 / n] * 4)
-    U.check(g, o, U.fields(wl), shocked=False, what=f"euler1d n={n} bc={bc}")
+    U.check(g, o, U.fields(wl), shocked=False, what=f"euler1d n={n} bc={bc}", wl=wl)
 
 
 def test_euler1d_example_5_2_run():
     wl = WL.euler1d_sine(40)
     g, o, (t, n), (t_o, n_o) = U.run_both(wl, 1.0)
     assert n == n_o and t == t_o == 1.0
-    U.check(g, o, U.fields(wl), shocked=False, what="euler1d sine")
+    U.check(g, o, U.fields(wl), shocked=False, what="euler1d sine", wl=wl)
 
 
 @pytest.mark.parametrize("maker", [lambda: WL.sod(100), lambda: WL.lax(200), lambda: WL.random_riemann1d(3, nx=257)])
@@ -53,7 +53,7 @@ def test_euler1d_shocked_runs(maker):
     T = min(wl.t_final, 0.05 if wl.name.startswith("riemann") else wl.t_final)
     g, o, (t, n), (t_o, n_o) = U.run_both(wl, T)
     assert n == n_o
-    U.check(g, o, U.fields(wl), shocked=True, what=wl.name)
+    U.check(g, o, U.fields(wl), shocked=True, what=wl.name, wl=wl)
 
 
 def test_linear_weights_mode():
@@ -62,12 +62,19 @@ def test_linear_weights_mode():
     wl.domain = (0.0, 1.0, 0.0, 1.0)
     wl.state = {"W": W, "V": V}
     g, o = U.steps_both(wl, [0.002] * 3, flag_mode=1, linear=True)
-    U.check(g, o, U.fields(wl), shocked=False, what="linear weights")
+    U.check(g, o, U.fields(wl), shocked=False, what="linear weights", wl=wl)
 
 
 def test_per_cell_flags():
+    """Random flags in smooth regions, nonlinear weights kept within four cells of the jump."""
     wl = WL.sod(64)
     rng = np.random.default_rng(1)
     flag = (rng.random(64) < 0.5).astype(np.uint8)
+    flag[28:36] = 1
     g, o = U.steps_both(wl, [0.004] * 3, flag=flag, flag_mode=2)
-    U.check(g, o, U.fields(wl), shocked=True, what="per-cell flags")
+    U.check(g, o, U.fields(wl), shocked=True, what="per-cell flags", wl=wl)
+    W, V = WL.random_smooth_1d(12, 64)
+    wl.state = {"W": W, "V": V}
+    flag = (rng.random(64) < 0.5).astype(np.uint8)
+    g, o = U.steps_both(wl, [0.002] * 3, flag=flag, flag_mode=2)
+    U.check(g, o, U.fields(wl), shocked=False, what="per-cell flags, smooth", wl=wl)
