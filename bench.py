@@ -161,7 +161,8 @@ def bench_gpu(args):
     cells = wl.nx * wl.ny
     stream = torch.cuda.Stream()
     sol = S.Solver(2, S.EULER, n, n, wl.domain, wl.bc, stream=stream.cuda_stream)
-    dev = {k: torch.from_numpy(v).cuda() for k, v in wl.state.items()}
+    dev = {k: torch.from_numpy(np.array(v)).cuda() for k, v in wl.state.items()}
+    torch.cuda.synchronize()  # the copies ran on the default stream; the solver uses `stream`
     sol.set_state(dev)
     torch.cuda.synchronize()
 
