@@ -161,6 +161,29 @@ typedef void* (*shweno_alloc_fn)(size_t bytes, void* ctx);
 typedef void (*shweno_free_fn)(void* ptr, void* ctx);
 shweno_status shweno_set_allocator(shweno_alloc_fn alloc, shweno_free_fn release, void* ctx);
 
+/* Allocation-free single 1D step.  The paper has no counterpart: this is a convenience for
+ * callers that cannot allocate device memory when they step -- code running inside an open
+ * CUDA stream capture (allocation is not capturable and synchronises the device), real-time
+ * loops that cannot take an allocation's latency, and frameworks that own all device memory
+ * through their own pool.  It advances one 1D state by dt (Section 2 scheme, same kernels as
+ * shweno_step) without any allocation: the step's scratch (per-face fluxes and states and the
+ * kernels' control block) lives in one fixed __device__ array of 256 bytes + 48 (nx_max + 1)
+ * bytes (about 3.1 MB) that every GPU loading this library holds until exit.
+ *   eq, nx (4 <= nx <= SHWENO_NOALLOC_MAX_NX), [x0, x1], gamma, bc_kind[2] (x-low, x-high;
+ *   PERIODIC, OUTFLOW, REFLECTIVE or INFLOW), inflow[2][4] (may be NULL), flag_mode 0 or 1;
+ *   state_in / state_out: device pointers to [2][ncomp][nx] float64 (W then V), not
+ *   overlapping; t: time of state_in; dt > 0; cuda_stream: the stream the work is ordered on.
+ * The call waits for the step and returns NONPHYSICAL if the new state has rho <= 0, p <= 0 or
+ * a NaN (state_out then holds that state; state_in is untouched).  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress, with that device current) and
+ * caches it, so it should come before any stream capture.  All calls share the one array: calls
+ * that overlap on the GPU race.  Sizes beyond the maximum return INVALID. */
+#define SHWENO_NOALLOC_MAX_NX 65536
+shweno_status shweno_step1d_noalloc(int32_t eq, int64_t nx, double x0, double x1, double gamma,
+                                    const int32_t bc_kind[2], const double inflow[2][4],
+                                    int32_t flag_mode, const double* state_in, double* state_out,
+                                    double t, double dt, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

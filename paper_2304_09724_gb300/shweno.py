@@ -45,7 +45,8 @@ class ShwenoError(RuntimeError):
 EXPORTS = ["shweno_create", "shweno_set_state", "shweno_get_state", "shweno_step", "shweno_run",
            "shweno_advance", "shweno_sync", "shweno_set_timing", "shweno_get_timing",
            "shweno_kernel_name", "shweno_cfl_dt", "shweno_get_time", "shweno_set_flags",
-           "shweno_destroy", "shweno_last_error", "shweno_set_allocator"]
+           "shweno_destroy", "shweno_last_error", "shweno_set_allocator", "shweno_step1d_noalloc"]
+NOALLOC_MAX_NX = 65536
 
 _lib = None
 
@@ -77,6 +78,10 @@ def lib():
     L.shweno_kernel_name.argtypes = [vp, ctypes.c_int]
     L.shweno_kernel_name.restype = ctypes.c_char_p
     L.shweno_set_allocator.argtypes = [vp, vp, vp]
+    L.shweno_step1d_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_double * 4), ctypes.c_int32, vp, vp,
+                                        ctypes.c_double, ctypes.c_double, vp]
     L.shweno_last_error.argtypes = [vp]
     L.shweno_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -174,6 +179,15 @@ def shweno_get_timing(h, max_kernels=8):
     _check(lib().shweno_get_timing(h, ms, max_kernels, ctypes.byref(nk), ctypes.byref(ns)), h)
     names = [lib().shweno_kernel_name(h, k).decode() for k in range(nk.value)]
     return {n: ms[k] for k, n in enumerate(names)}, ns.value
+
+
+def shweno_step1d_noalloc(eq, nx, x0, x1, gamma, bc, inflow, flag_mode, state_in, state_out, t, dt,
+                          stream=0):
+    """One 1D step without any device allocation (see include/shweno.h); returns the status."""
+    kinds = (ctypes.c_int32 * 2)(*bc)
+    infl = ((ctypes.c_double * 4) * 2)(*[(ctypes.c_double * 4)(*inflow[s]) for s in range(2)]) if inflow else None
+    return lib().shweno_step1d_noalloc(eq, nx, x0, x1, gamma, kinds, infl, flag_mode, _ptr(state_in)[0],
+                                       _ptr(state_out)[0], t, dt, stream or None)
 
 
 def shweno_destroy(h):
