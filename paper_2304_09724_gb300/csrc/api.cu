@@ -283,6 +283,7 @@ shweno_status shweno_create(const shweno_grid* grid, double gamma, const shweno_
   P.eps = o.eps;
   for (int k = 0; k < 3; ++k) P.gam[k] = o.gam[k];
   P.flag_mode = o.flag_mode;
+  shweno::set_ck_factors(P);
 
   h->cells = (size_t)P.nx * P.ny;
   h->nfields = dim == 2 ? 4 : 2;
@@ -305,7 +306,10 @@ shweno_status shweno_create(const shweno_grid* grid, double gamma, const shweno_
   const size_t scr = dim == 2 ? shweno::scratch2d_doubles(P) : 2 * (size_t)P.ncomp * (P.nx + 1);
   h->scratch = (double*)dev_alloc(scr * sizeof(double));
   if (!h->scratch) return bail(SHWENO_E_NOMEM, "device allocation of the step scratch failed");
-  if (dim == 2) h->S = shweno::carve_scratch2d(P, h->scratch);
+  if (dim == 2) {
+    h->S = shweno::carve_scratch2d(P, h->scratch);
+    shweno::init_kernels2d();
+  }
   else { h->FH = h->scratch; h->WE = h->scratch + (size_t)P.ncomp * (P.nx + 1); }
   h->ctl = (Ctl*)dev_alloc(sizeof(Ctl));
   if (!h->ctl) return bail(SHWENO_E_NOMEM, "device allocation of the control block failed");

@@ -30,6 +30,13 @@ def derive():
     for k in range(5):
         e = sp.expand(sol[c[k]].subs(sub))
         coef[k] = {v: e.coeff(v) for v in (W0, s, dv, a, sv)}
+    # normalised Taylor coefficients of p1 at xi = +1/2 and -1/2 as linear forms in the data
+    P1 = P.subs(sol)
+    ends = {}
+    for tag, x0 in (("P", half), ("M", -half)):
+        for m in range(5):
+            e = sp.expand(sp.diff(P1, xi, m).subs(xi, x0) / sp.factorial(m))
+            ends[(tag, m)] = {v: e.coeff(v) for v in (Wm, W0, Wp, vm, vp)}
     # smoothness indicator of p1 as a quadratic form in c1..c4
     cc = sp.symbols("k0:5")
     Pc = sum(cc[k] * xi ** k for k in range(5))
@@ -38,7 +45,7 @@ def derive():
     for i in range(1, 5):
         for j in range(i, 5):
             bq[(i, j)] = beta.coeff(cc[i], 1).coeff(cc[j], 1) if i != j else beta.coeff(cc[i], 2)
-    return coef, bq, (W0, s, dv, a, sv)
+    return coef, bq, (W0, s, dv, a, sv), ends, (Wm, W0, Wp, vm, vp)
 
 
 def frac(r):
@@ -49,7 +56,7 @@ def frac(r):
 
 
 def main():
-    coef, bq, names = derive()
+    coef, bq, names, ends, data = derive()
     g = sp.sqrt(sp.Rational(15)) / 10  # Gauss node offset in [-1/2,1/2]
     lines = [
         "// Generated by gen_tables.py -- exact rational constants of the SHWENO reconstruction.",
@@ -61,6 +68,23 @@ def main():
     for k in range(5):
         for v in names:
             lines.append(f"constexpr double P1_C{k}_{v} = {frac(coef[k][v])};")
+    lines.append("// Taylor coefficient m (d^m p1/dxi^m / m!) at xi = +1/2 (P) and -1/2 (M):")
+    lines.append("// END_<P|M>[m][v] over the data v = (W-, W0, W+, v-, v+)")
+    for tag in ("P", "M"):
+        for m in range(5):
+            for iv, v in enumerate(data):
+                lines.append(f"constexpr double END_{tag}_{m}_{iv} = {frac(ends[(tag, m)][v])};")
+    lines.append("// dot product of row p of END_P (plus) or END_M with the data d[0..4]")
+    lines.append("template <bool PLUS>")
+    lines.append("__host__ __device__ __forceinline__ double end_dot(int p, const double d[5]) {")
+    lines.append("  switch (p) {")
+    for m in range(5):
+        tp = " + ".join(f"END_P_{m}_{iv} * d[{iv}]" for iv in range(5))
+        tm = " + ".join(f"END_M_{m}_{iv} * d[{iv}]" for iv in range(5))
+        lines.append(f"    case {m}: return PLUS ? ({tp}) : ({tm});")
+    lines.append("  }")
+    lines.append("  return 0.0;")
+    lines.append("}")
     lines.append("// smoothness indicator of p1: beta1 = sum_{i<=j} B_ij c_i c_j (i, j >= 1)")
     for (i, j), val in bq.items():
         lines.append(f"constexpr double BETA_{i}{j} = {frac(val)};")

@@ -28,6 +28,70 @@ constexpr double P1_C4_s = (-1.0 / 2.0);
 constexpr double P1_C4_dv = (1.0 / 4.0);
 constexpr double P1_C4_a = 0.0;
 constexpr double P1_C4_sv = 0.0;
+// Taylor coefficient m (d^m p1/dxi^m / m!) at xi = +1/2 (P) and -1/2 (M):
+// END_<P|M>[m][v] over the data v = (W-, W0, W+, v-, v+)
+constexpr double END_P_0_0 = (-23.0 / 120.0);
+constexpr double END_P_0_1 = (19.0 / 30.0);
+constexpr double END_P_0_2 = (67.0 / 120.0);
+constexpr double END_P_0_3 = (-3.0 / 40.0);
+constexpr double END_P_0_4 = (-7.0 / 40.0);
+constexpr double END_P_1_0 = (3.0 / 8.0);
+constexpr double END_P_1_1 = -2.0;
+constexpr double END_P_1_2 = (13.0 / 8.0);
+constexpr double END_P_1_3 = (1.0 / 8.0);
+constexpr double END_P_1_4 = (-3.0 / 8.0);
+constexpr double END_P_2_0 = (7.0 / 8.0);
+constexpr double END_P_2_1 = -1.0;
+constexpr double END_P_2_2 = (1.0 / 8.0);
+constexpr double END_P_2_3 = (3.0 / 8.0);
+constexpr double END_P_2_4 = (3.0 / 8.0);
+constexpr double END_P_3_0 = (-3.0 / 4.0);
+constexpr double END_P_3_1 = 2.0;
+constexpr double END_P_3_2 = (-5.0 / 4.0);
+constexpr double END_P_3_3 = (-1.0 / 4.0);
+constexpr double END_P_3_4 = (3.0 / 4.0);
+constexpr double END_P_4_0 = (-1.0 / 2.0);
+constexpr double END_P_4_1 = 1.0;
+constexpr double END_P_4_2 = (-1.0 / 2.0);
+constexpr double END_P_4_3 = (-1.0 / 4.0);
+constexpr double END_P_4_4 = (1.0 / 4.0);
+constexpr double END_M_0_0 = (67.0 / 120.0);
+constexpr double END_M_0_1 = (19.0 / 30.0);
+constexpr double END_M_0_2 = (-23.0 / 120.0);
+constexpr double END_M_0_3 = (7.0 / 40.0);
+constexpr double END_M_0_4 = (3.0 / 40.0);
+constexpr double END_M_1_0 = (-13.0 / 8.0);
+constexpr double END_M_1_1 = 2.0;
+constexpr double END_M_1_2 = (-3.0 / 8.0);
+constexpr double END_M_1_3 = (-3.0 / 8.0);
+constexpr double END_M_1_4 = (1.0 / 8.0);
+constexpr double END_M_2_0 = (1.0 / 8.0);
+constexpr double END_M_2_1 = -1.0;
+constexpr double END_M_2_2 = (7.0 / 8.0);
+constexpr double END_M_2_3 = (-3.0 / 8.0);
+constexpr double END_M_2_4 = (-3.0 / 8.0);
+constexpr double END_M_3_0 = (5.0 / 4.0);
+constexpr double END_M_3_1 = -2.0;
+constexpr double END_M_3_2 = (3.0 / 4.0);
+constexpr double END_M_3_3 = (3.0 / 4.0);
+constexpr double END_M_3_4 = (-1.0 / 4.0);
+constexpr double END_M_4_0 = (-1.0 / 2.0);
+constexpr double END_M_4_1 = 1.0;
+constexpr double END_M_4_2 = (-1.0 / 2.0);
+constexpr double END_M_4_3 = (-1.0 / 4.0);
+constexpr double END_M_4_4 = (1.0 / 4.0);
+// dot product of row p of END_P (plus) or END_M with the data d[0..4]
+template <bool PLUS>
+__host__ __device__ __forceinline__ double end_dot(int p, const double d[5]) {
+  switch (p) {
+    case 0: return PLUS ? (END_P_0_0 * d[0] + END_P_0_1 * d[1] + END_P_0_2 * d[2] + END_P_0_3 * d[3] + END_P_0_4 * d[4]) : (END_M_0_0 * d[0] + END_M_0_1 * d[1] + END_M_0_2 * d[2] + END_M_0_3 * d[3] + END_M_0_4 * d[4]);
+    case 1: return PLUS ? (END_P_1_0 * d[0] + END_P_1_1 * d[1] + END_P_1_2 * d[2] + END_P_1_3 * d[3] + END_P_1_4 * d[4]) : (END_M_1_0 * d[0] + END_M_1_1 * d[1] + END_M_1_2 * d[2] + END_M_1_3 * d[3] + END_M_1_4 * d[4]);
+    case 2: return PLUS ? (END_P_2_0 * d[0] + END_P_2_1 * d[1] + END_P_2_2 * d[2] + END_P_2_3 * d[3] + END_P_2_4 * d[4]) : (END_M_2_0 * d[0] + END_M_2_1 * d[1] + END_M_2_2 * d[2] + END_M_2_3 * d[3] + END_M_2_4 * d[4]);
+    case 3: return PLUS ? (END_P_3_0 * d[0] + END_P_3_1 * d[1] + END_P_3_2 * d[2] + END_P_3_3 * d[3] + END_P_3_4 * d[4]) : (END_M_3_0 * d[0] + END_M_3_1 * d[1] + END_M_3_2 * d[2] + END_M_3_3 * d[3] + END_M_3_4 * d[4]);
+    case 4: return PLUS ? (END_P_4_0 * d[0] + END_P_4_1 * d[1] + END_P_4_2 * d[2] + END_P_4_3 * d[3] + END_P_4_4 * d[4]) : (END_M_4_0 * d[0] + END_M_4_1 * d[1] + END_M_4_2 * d[2] + END_M_4_3 * d[3] + END_M_4_4 * d[4]);
+  }
+  return 0.0;
+}
 // smoothness indicator of p1: beta1 = sum_{i<=j} B_ij c_i c_j (i, j >= 1)
 constexpr double BETA_11 = 1.0;
 constexpr double BETA_12 = 0.0;

@@ -27,7 +27,18 @@ struct Params {
   double eps;             // epsilon of the nonlinear weights
   double gam[3];          // linear weights
   int32_t flag_mode;      // FLAG_*
+  // Cauchy-Kovalevskaya scale factors (m+1)/((k+1) dx) and (n+1)/((k+1) dy), set by the host
+  double ckx[5][4], cky[5][4];
 };
+
+// Fills Params::ckx / cky from dx, dy.
+inline void set_ck_factors(Params& P) {
+  for (int m = 0; m < 5; ++m)
+    for (int k = 0; k < 4; ++k) {
+      P.ckx[m][k] = (m + 1) / ((k + 1) * P.dx);
+      P.cky[m][k] = (m + 1) / ((k + 1) * P.dy);
+    }
+}
 
 // Device-resident time-stepping control block.  One step = begin_step, the step kernels,
 // end_step; only begin_step/end_step (one thread each) write it, the step kernels only read.

@@ -29,6 +29,7 @@ void launch_step2d(const Params& P, Ctl* ctl, const double* s0, const double* s1
                    double* o1, const uint8_t* flag, const Scratch2D& S, cudaStream_t st,
                    cudaEvent_t* ev);
 size_t scratch2d_doubles(const Params& P);
+void init_kernels2d();  // kernel attributes (dynamic shared memory); call before any capture
 Scratch2D carve_scratch2d(const Params& P, double* base);
 void launch_begin_step(Ctl* ctl, cudaStream_t st);
 void launch_end_step(Ctl* ctl, cudaStream_t st);

@@ -101,47 +101,72 @@ __global__ void __launch_bounds__(TX * TY) coef2d_kernel(Params P, const Ctl* __
 }
 
 // ------------------------------------------------------------------ one face point
-// Second pass across the face for one side.  ev[set*4+q][k][col] holds the first-pass
-// Taylor coefficients (order k along the face) of the three stencil columns c0..c0+2; the
-// weights come from the order-0 data and serve every order (remark ending Section 2.1.2).
-struct SideMix { Mix m[4]; };
+// Second pass across the face.  ev[set*4+q][k][col] holds the first-pass Taylor coefficients
+// (order k along the face) of a row of stencil columns.  Each cell's weights come from its
+// order-0 data and serve every order (remark ending Section 2.1.2) and both of the cell's faces:
+// they are computed once per cell (cell_mixes) into shared memory.
+struct MixTable {
+  double A[4][SPAN], B[4][SPAN], C[4][SPAN];  // p = A p1 + B p2 + C p3 per (comp, cell column)
+};
 
-__device__ __forceinline__ void side_weights(const Params& P, const double (*ev)[5][SPAN], int c0,
-                                             int nonlinear, SideMix& sm) {
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const double Wm = ev[q][0][c0], W0 = ev[q][0][c0 + 1], Wp = ev[q][0][c0 + 2];
-    double c[5];
-    p1_coeffs(Wm, W0, Wp, ev[4 + q][0][c0], ev[4 + q][0][c0 + 2], c);
-    sm.m[q] = shweno_mix(P, Wm, W0, Wp, c, nonlinear);
+constexpr size_t kEvBytes = sizeof(double) * 8 * 5 * SPAN;
+constexpr size_t kFaceSmem = kEvBytes + sizeof(MixTable);
+
+// Weights of the cells in columns 1..SEG+1 (the cells whose faces the CTA owns).  nl(col)
+// returns whether the cell of column col uses the nonlinear weights.
+template <typename FlagOf>
+__device__ __forceinline__ void cell_mixes(const Params& P, const double (*ev)[5][SPAN],
+                                           MixTable& mt, FlagOf nl) {
+  for (int it = threadIdx.x; it < 4 * (SEG + 1); it += SEG) {
+    const int q = it / (SEG + 1), c = 1 + it % (SEG + 1);
+    const double Wm = ev[q][0][c - 1], W0 = ev[q][0][c], Wp = ev[q][0][c + 1];
+    double cf[5];
+    p1_coeffs(Wm, W0, Wp, ev[4 + q][0][c - 1], ev[4 + q][0][c + 1], cf);
+    const Mix m = shweno_mix(P, Wm, W0, Wp, cf, nl(c));
+    mt.A[q][c] = m.A;
+    mt.B[q][c] = m.B;
+    mt.C[q][c] = m.C;
   }
 }
 
-// Cross-face Taylor coefficients e[p] (p <= 4 - k) of tangential order k, component q.
-__device__ __forceinline__ void side_column(const double (*ev)[5][SPAN], int c0, const Mix& mx,
-                                            int q, int k, double xi0, double e[5]) {
-  const double Wm = ev[q][k][c0], W0 = ev[q][k][c0 + 1], Wp = ev[q][k][c0 + 2];
-  double c[5];
-  p1_coeffs(Wm, W0, Wp, ev[4 + q][k][c0], ev[4 + q][k][c0 + 2], c);
-  mix_coeffs(mx, Wm, W0, Wp, c, e);
-  taylor_shift2(e, xi0, 4 - k);
+// Cross-face Taylor coefficients e[p] (p <= 4 - k) of tangential order k, component q, of the
+// cell in column c0 + 1 (stencil c0..c0+2), at its right end (PLUS, xi = +1/2) or left end:
+//   e[p] = A * END[p] . data + (small-stencil terms for p <= 1),
+// with END the constant rows of p1's Taylor coefficients at the end and data = (W-, W0, W+,
+// v-, v+) of order k.
+template <bool PLUS>
+__device__ __forceinline__ void side_out(const double (*ev)[5][SPAN], int c0, int q, int k, double A,
+                                         double B, double C, double e[5]) {
+  using namespace shweno_tables;
+  const double d[5] = {ev[q][k][c0], ev[q][k][c0 + 1], ev[q][k][c0 + 2], ev[4 + q][k][c0],
+                       ev[4 + q][k][c0 + 2]};
+#pragma unroll
+  for (int p = 0; p + k <= 4; ++p) e[p] = A * end_dot<PLUS>(p, d);
+  // p2 = W0 + (W0 - W-) xi and p3 = W0 + (W+ - W0) xi: value and slope at the end
+  if (PLUS) e[0] += (1.5 * B + 0.5 * C) * d[1] - 0.5 * B * d[0] + 0.5 * C * d[2];
+  else e[0] += (0.5 * B + 1.5 * C) * d[1] + 0.5 * B * d[0] - 0.5 * C * d[2];
+  if (k <= 3) e[1] += (B - C) * d[1] - B * d[0] + C * d[2];
 }
 
 // Face point: both sides' second pass, HLLC, upwinding, CK; returns the time-Taylor
-// coefficients tc[q][0..4].  dir = 0: x-face (first pass along y), 1: y-face.
-__device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5][SPAN], int c0,
-                                           int nlL, int nlR, int dir, double tc[4][5]) {
+// coefficients tc[q][0..4].  Left cell in column c0 + 1, right cell in c0 + 2.  dir = 0: x-face
+// (first pass along y), 1: y-face.
+__device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5][SPAN],
+                                           const MixTable& mt, int c0, int dir, double tc[4][5]) {
   const double g = P.gamma;
-  SideMix L, R;
-  side_weights(P, ev, c0, nlL, L);
-  side_weights(P, ev, c0 + 1, nlR, R);
   double a[4][25];
   double dl[4][5], dr[4][5];
+  double AL[4], BL[4], CL[4], AR[4], BR[4], CR[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    AL[q] = mt.A[q][c0 + 1]; BL[q] = mt.B[q][c0 + 1]; CL[q] = mt.C[q][c0 + 1];
+    AR[q] = mt.A[q][c0 + 2]; BR[q] = mt.B[q][c0 + 2]; CR[q] = mt.C[q][c0 + 2];
+  }
   // tangential order 0 first: it carries the leading-term data
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    side_column(ev, c0, L.m[q], q, 0, 0.5, dl[q]);
-    side_column(ev, c0 + 1, R.m[q], q, 0, -0.5, dr[q]);
+    side_out<true>(ev, c0, q, 0, AL[q], BL[q], CL[q], dl[q]);
+    side_out<false>(ev, c0 + 1, q, 0, AR[q], BR[q], CR[q], dr[q]);
   }
   double WL[4], WR[4], Ws[4];
 #pragma unroll
@@ -154,8 +179,8 @@ __device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5
     if (k > 0) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        side_column(ev, c0, L.m[q], q, k, 0.5, dl[q]);
-        side_column(ev, c0 + 1, R.m[q], q, k, -0.5, dr[q]);
+        side_out<true>(ev, c0, q, k, AL[q], BL[q], CL[q], dl[q]);
+        side_out<false>(ev, c0 + 1, q, k, AR[q], BR[q], CR[q], dr[q]);
       }
     }
 #pragma unroll
@@ -173,17 +198,8 @@ __device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) a[q][0] = Ws[q];
-  double cx[5][4], cy[5][4];
-  const double ihx = 1.0 / P.dx, ihy = 1.0 / P.dy;
-#pragma unroll
-  for (int m = 0; m < 5; ++m)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      cx[m][k] = (m + 1) * ihx / (k + 1);
-      cy[m][k] = (m + 1) * ihy / (k + 1);
-    }
   double t4[4][5];
-  ck_euler2d(a, t4, cx, cy, g - 1.0);
+  ck_euler2d(a, t4, P.ckx, P.cky, g - 1.0);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     tc[q][0] = Ws[q];
@@ -228,7 +244,9 @@ __global__ void __launch_bounds__(SEG) xface2d_kernel(Params P, const Ctl* __res
                                                       double* __restrict__ FX,
                                                       double* __restrict__ WX,
                                                       double* __restrict__ WC) {
-  __shared__ double ev[8][5][SPAN];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double(*ev)[5][SPAN] = reinterpret_cast<double(*)[5][SPAN]>(smem_raw);
+  MixTable& mt = *reinterpret_cast<MixTable*>(smem_raw + kEvBytes);
   if (!ctl->active) return;
   const int slice = blockIdx.z;  // 0..2: Gauss point of the rows; 3: corner rows
   const int row = blockIdx.y;    // Gauss: cell row j; corner: corner row jc (y_{jc-1/2})
@@ -239,9 +257,9 @@ __global__ void __launch_bounds__(SEG) xface2d_kernel(Params P, const Ctl* __res
   for (int it = threadIdx.x; it < 8 * SPAN; it += SEG) {
     const int col = it % SPAN, rq = it / SPAN;
     const int tcol = f0 + col;
-    if (tcol >= NX4) continue;
-    double e[5];
-    if (slice < 3) {
+    double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (tcol >= NX4) {
+    } else if (slice < 3) {
       const double* src = ycoef + ((size_t)(rq * 5) * NY2 + (row + 1)) * NX4 + tcol;
 #pragma unroll
       for (int k = 0; k < 5; ++k) e[k] = src[(size_t)k * NY2 * NX4];
@@ -261,18 +279,17 @@ __global__ void __launch_bounds__(SEG) xface2d_kernel(Params P, const Ctl* __res
     for (int k = 0; k < 5; ++k) ev[rq][k][col] = e[k];
   }
   __syncthreads();
+  // cell column c holds cell i = f0 + c - 2; a corner row uses the rows below and above
+  cell_mixes(P, ev, mt, [&](int c) {
+    const int i = f0 + c - 2;
+    return slice < 3 ? cell_flag(P, flag, i, row)
+                     : (cell_flag(P, flag, i, row - 1) | cell_flag(P, flag, i, row));
+  });
+  __syncthreads();
   const int fi = f0 + threadIdx.x;  // face x_{fi-1/2}
   if (fi > P.nx) return;
-  int nlL, nlR;
-  if (slice < 3) {
-    nlL = cell_flag(P, flag, fi - 1, row);
-    nlR = cell_flag(P, flag, fi, row);
-  } else {
-    nlL = cell_flag(P, flag, fi - 1, row - 1) | cell_flag(P, flag, fi - 1, row);
-    nlR = cell_flag(P, flag, fi, row - 1) | cell_flag(P, flag, fi, row);
-  }
   double tc[4][5];
-  face_point(P, ev, threadIdx.x, nlL, nlR, 0, tc);
+  face_point(P, ev, mt, threadIdx.x, 0, tc);
   const double dt = ctl->dt;
   if (slice < 3) {
     double Fh[4], We[4];
@@ -295,7 +312,9 @@ __global__ void __launch_bounds__(SEG) yface2d_kernel(Params P, const Ctl* __res
                                                       const uint8_t* __restrict__ flag,
                                                       double* __restrict__ FY,
                                                       double* __restrict__ WY) {
-  __shared__ double ev[8][5][SPAN];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double(*ev)[5][SPAN] = reinterpret_cast<double(*)[5][SPAN]>(smem_raw);
+  MixTable& mt = *reinterpret_cast<MixTable*>(smem_raw + kEvBytes);
   if (!ctl->active) return;
   const int slice = blockIdx.z;  // Gauss point of the columns
   const int col = blockIdx.y;    // cell column i
@@ -305,22 +324,23 @@ __global__ void __launch_bounds__(SEG) yface2d_kernel(Params P, const Ctl* __res
   for (int it = threadIdx.x; it < 8 * SPAN; it += SEG) {
     const int r = it % SPAN, rq = it / SPAN;
     const int trow = f0 + r;
-    if (trow >= NY4) continue;
-    double e[5];
-    const double* src = xcoef + ((size_t)(rq * 5) * P.nx + col) * NY4 + trow;
+    double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (trow < NY4) {
+      const double* src = xcoef + ((size_t)(rq * 5) * P.nx + col) * NY4 + trow;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) e[k] = src[(size_t)k * P.nx * NY4];
-    if (slice != 1) taylor_shift2(e, slice == 0 ? -GAUSS_G : GAUSS_G, 4);
+      for (int k = 0; k < 5; ++k) e[k] = src[(size_t)k * P.nx * NY4];
+      if (slice != 1) taylor_shift2(e, slice == 0 ? -GAUSS_G : GAUSS_G, 4);
+    }
 #pragma unroll
     for (int k = 0; k < 5; ++k) ev[rq][k][r] = e[k];
   }
   __syncthreads();
+  cell_mixes(P, ev, mt, [&](int c) { return cell_flag(P, flag, col, f0 + c - 2); });
+  __syncthreads();
   const int fj = f0 + threadIdx.x;  // face y_{fj-1/2}
   if (fj > P.ny) return;
-  const int nlB = cell_flag(P, flag, col, fj - 1);
-  const int nlT = cell_flag(P, flag, col, fj);
   double tc[4][5];
-  face_point(P, ev, threadIdx.x, nlB, nlT, 1, tc);
+  face_point(P, ev, mt, threadIdx.x, 1, tc);
   double Gh[4], We[4];
   lobatto(tc, ctl->dt, P.gamma, 1, Gh, We);
 #pragma unroll
@@ -404,6 +424,11 @@ Scratch2D carve_scratch2d(const Params& P, double* base) {
   return S;
 }
 
+void init_kernels2d() {
+  cudaFuncSetAttribute(xface2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
+  cudaFuncSetAttribute(yface2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
+}
+
 void launch_step2d(const Params& P, Ctl* ctl, const double* s0, const double* s1, double* o0,
                    double* o1, const uint8_t* flag, const Scratch2D& S, cudaStream_t st,
                    cudaEvent_t* ev) {
@@ -412,10 +437,10 @@ void launch_step2d(const Params& P, Ctl* ctl, const double* s0, const double* s1
   coef2d_kernel<<<cg, cb, 0, st>>>(P, ctl, s0, s1, flag, S.ycoef, S.xcoef);
   if (ev) cudaEventRecord(ev[1], st);
   dim3 xg((P.nx + 1 + SEG - 1) / SEG, P.ny + 1, 4);
-  xface2d_kernel<<<xg, SEG, 0, st>>>(P, ctl, S.ycoef, flag, S.FX, S.WX, S.WC);
+  xface2d_kernel<<<xg, SEG, kFaceSmem, st>>>(P, ctl, S.ycoef, flag, S.FX, S.WX, S.WC);
   if (ev) cudaEventRecord(ev[2], st);
   dim3 yg((P.ny + 1 + SEG - 1) / SEG, P.nx, 3);
-  yface2d_kernel<<<yg, SEG, 0, st>>>(P, ctl, S.xcoef, flag, S.FY, S.WY);
+  yface2d_kernel<<<yg, SEG, kFaceSmem, st>>>(P, ctl, S.xcoef, flag, S.FY, S.WY);
   if (ev) cudaEventRecord(ev[3], st);
   dim3 ug((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
   update2d_kernel<<<ug, cb, 0, st>>>(P, ctl, s0, s1, o0, o1, S.FX, S.WX, S.FY, S.WY, S.WC);
