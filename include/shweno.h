@@ -161,6 +161,52 @@ typedef void* (*shweno_alloc_fn)(size_t bytes, void* ctx);
 typedef void (*shweno_free_fn)(void* ptr, void* ctx);
 shweno_status shweno_set_allocator(shweno_alloc_fn alloc, shweno_free_fn release, void* ctx);
 
+/* ---------------------------------------------------------------- learned troubled-cell flag
+ * Not in the paper: a small network decides per cell whether the reconstructions anchored on it
+ * need the nonlinear SHWENO weights (flag 1) or may use the linear weights (flag 0, which makes
+ * them exactly the big-stencil quartic p1 of Section 2.4 and skips the smoothness indicators).
+ * Network: SHWENO_FLAG_FEATURES inputs -> 32 (ReLU) -> 32 (ReLU) -> 1 (sigmoid), FP32, parameters
+ * packed W1[32][22], b1[32], W2[32][32], b2[32], w3[32], b3 (SHWENO_FLAG_PARAMS floats).
+ * Features of a cell (2D Euler): for rho and E, the eight 3x3 neighbours minus the centre and
+ * dx*V, dy*Y of the centre, each divided by (stencil range + 1e-12 |centre| + 1e-300), and
+ * log10(range / (|centre| + 1e-30) + 1e-16) / 8; neighbour order (-1,-1), (0,-1), (1,-1), (-1,0),
+ * (1,0), (-1,1), (0,1), (1,1) as (di, dj).  All pointers of this group are device pointers. */
+#define SHWENO_FLAG_FEATURES 22
+#define SHWENO_FLAG_PARAMS 1825
+
+/* Features of the committed state: out[cells][SHWENO_FLAG_FEATURES] (2D Euler handles). */
+shweno_status shweno_flag_features(shweno_handle* h, float* out);
+
+/* Training-label source: per cell, max over its 16 first-pass reconstructions (y-pass on {W,Y}
+ * and {V,Z}, x-pass on {W,V} and {Y,Z}, every component) of max_l |w_l - gamma_l| / gamma_l, the
+ * relative deviation of the plain scheme's nonlinear weights from the linear ones.  out[cells]. */
+shweno_status shweno_weight_deviation(shweno_handle* h, double* out);
+
+/* Network on n samples: prob[b] = sigmoid(net(x[b])).  x: [n][SHWENO_FLAG_FEATURES]. */
+shweno_status shweno_mlp_forward(const float* params, const float* x, int64_t n, float* prob,
+                                 void* cuda_stream);
+
+/* Gradient of the mean weighted binary cross-entropy
+ *   L = mean_b( -pos_weight y_b log(sig(z_b)) - (1 - y_b) log(1 - sig(z_b)) ),  y_b in {0, 1},
+ * written to grad[SHWENO_FLAG_PARAMS] (overwritten) and L to *loss. */
+shweno_status shweno_mlp_grad(const float* params, const float* x, const float* y, int64_t n,
+                              float pos_weight, float* grad, float* loss, void* cuda_stream);
+
+/* One Adam step (bias-corrected; step counts from 1) on params with moment buffers m, v. */
+shweno_status shweno_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t step,
+                              float lr, float beta1, float beta2, float eps, void* cuda_stream);
+
+/* Puts a flag_mode-2 handle in learned mode: from now on every step first evaluates the network
+ * on every cell of the committed state, sets flag = (probability > threshold), dilates the flags
+ * by one cell (3x3 OR; imposed-state ghost cells count as troubled), then steps with those flags.
+ * params: SHWENO_FLAG_PARAMS floats (device if on_device, else host).  Errors: STATE if the
+ * handle was not created with flag_mode 2 or is 1D. */
+shweno_status shweno_set_flag_net(shweno_handle* h, const float* params, double threshold,
+                                  int on_device);
+
+/* Flags used by the last step (after dilation), [ny][nx] bytes. */
+shweno_status shweno_get_flags(shweno_handle* h, uint8_t* out, int on_device);
+
 /* Allocation-free single 1D step.  The paper has no counterpart: this is a convenience for
  * callers that cannot allocate device memory when they step -- code running inside an open
  * CUDA stream capture (allocation is not capturable and synchronises the device), real-time

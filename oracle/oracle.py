@@ -77,6 +77,8 @@ def lib():
         L.orc_step2d_cells.argtypes = [pp, dp, dp, dp, dp, u8p, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int32), dp]
         L.orc_run.restype = ctypes.c_int64
+        L.orc_weight_deviation2d.argtypes = [pp, dp, dp, dp, dp, ctypes.c_double, dp]
+        L.orc_features2d.argtypes = [pp, dp, dp, dp, dp, ctypes.c_double, dp]
         L.orc_step2d_window.argtypes = [pp, dp, dp, dp, dp, u8p, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
         _lib = L
@@ -236,6 +238,22 @@ def step2d_window(P, state, dt, i0, j0, w, h, t=0.0, flag=None):
     lib().orc_step2d_window(ctypes.byref(P), _dp(W), _dp(V), _dp(Y), _dp(Z), fp, t, dt, i0, j0, w, h,
                             _dp(out))
     return {k: out[f] for f, k in enumerate("WVYZ")}
+
+
+def weight_deviation2d(P, state, t=0.0):
+    """Per cell: max relative deviation of the 16 first-pass nonlinear weights from gamma [ny][nx]."""
+    W, V, Y, Z = (_f64(state[k]) for k in "WVYZ")
+    out = np.zeros((P.ny, P.nx))
+    lib().orc_weight_deviation2d(ctypes.byref(P), _dp(W), _dp(V), _dp(Y), _dp(Z), t, _dp(out))
+    return out
+
+
+def features2d(P, state, t=0.0):
+    """Per-cell flag-network inputs [ny*nx][22] (see shweno_oracle.cpp)."""
+    W, V, Y, Z = (_f64(state[k]) for k in "WVYZ")
+    out = np.zeros((P.ny * P.nx, 22))
+    lib().orc_features2d(ctypes.byref(P), _dp(W), _dp(V), _dp(Y), _dp(Z), t, _dp(out))
+    return out
 
 
 def run(P, state, t_final, cfl, flag=None, max_steps=10 ** 9):

@@ -1029,6 +1029,74 @@ void orc_step2d_cells(const orc_problem* P, const double* W, const double* V, co
   step2d_cells(S, dt, ncells, ij, out);
 }
 
+// ----- learned troubled-cell flag (not in the paper; the task's learned layer) -----
+// Label source: the largest relative deviation max_l |w_l - gamma_l| / gamma_l of the nonlinear
+// weights of the 16 first-pass reconstructions anchored on cell (i, j) (y-pass on {W,Y} and
+// {V,Z}, x-pass on {W,V} and {Y,Z}, four components) in the always-nonlinear scheme.
+void orc_weight_deviation2d(const orc_problem* P, const double* W, const double* V, const double* Y,
+                            const double* Z, double t, double* out) {
+  State S{P, {W, V, Y, Z}, nullptr, t};
+  const int nc = ncomp(*P);
+  for (int j = 0; j < P->ny; ++j)
+    for (int i = 0; i < P->nx; ++i) {
+      double dev = 0.0;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int set = 0; set < 2; ++set)
+          for (int q = 0; q < nc; ++q) {
+            // pass 0: along y, sets {W,Y}, {V,Z}; pass 1: along x, sets {W,V}, {Y,Z}
+            int fa = pass == 0 ? (set == 0 ? 0 : 1) : (set == 0 ? 0 : 2);
+            int fd = pass == 0 ? (set == 0 ? 2 : 3) : (set == 0 ? 1 : 3);
+            int di = pass == 1, dj = pass == 0;
+            double h = pass == 0 ? P->dy : P->dx;
+            double Wb[3] = {fetch(S, fa, q, i - di, j - dj), fetch(S, fa, q, i, j),
+                            fetch(S, fa, q, i + di, j + dj)};
+            double v[2] = {h * fetch(S, fd, q, i - di, j - dj), h * fetch(S, fd, q, i + di, j + dj)};
+            double w[3];
+            shweno_weights(Wb, v, 0, P->eps, P->gam, w);
+            for (int l = 0; l < 3; ++l) dev = std::fmax(dev, std::fabs(w[l] - P->gam[l]) / P->gam[l]);
+          }
+      out[(size_t)j * P->nx + i] = dev;
+    }
+}
+
+// Features of cell (i, j), 11 per variable for rho (component 0) and E (last component):
+// the eight 3x3-stencil neighbours minus the centre and dx V, dy Y of the centre, all divided by
+// s = (max - min over the stencil) + 1e-12 |centre| + 1e-300; then log10(range/(|centre| +
+// 1e-30) + 1e-16) / 8.  Neighbour order: (-1,-1), (0,-1), (1,-1), (-1,0), (1,0), (-1,1), (0,1),
+// (1,1) as (di, dj).  out[cell][22].
+void orc_features2d(const orc_problem* P, const double* W, const double* V, const double* Y,
+                    const double* Z, double t, double* out) {
+  State S{P, {W, V, Y, Z}, nullptr, t};
+  const int nc = ncomp(*P);
+  const int comps[2] = {0, nc - 1};
+  for (int j = 0; j < P->ny; ++j)
+    for (int i = 0; i < P->nx; ++i) {
+      double* f = out + ((size_t)j * P->nx + i) * 22;
+      for (int a = 0; a < 2; ++a) {
+        const int q = comps[a];
+        double vals[3][3];
+        double mn = 1e300, mx = -1e300;
+        for (int dj = -1; dj <= 1; ++dj)
+          for (int di = -1; di <= 1; ++di) {
+            double x = fetch(S, 0, q, i + di, j + dj);
+            vals[dj + 1][di + 1] = x;
+            mn = std::fmin(mn, x);
+            mx = std::fmax(mx, x);
+          }
+        const double c = vals[1][1];
+        const double range = mx - mn;
+        const double sc = range + 1e-12 * std::fabs(c) + 1e-300;
+        int k = 0;
+        for (int dj = -1; dj <= 1; ++dj)
+          for (int di = -1; di <= 1; ++di)
+            if (di != 0 || dj != 0) f[a * 11 + k++] = (vals[dj + 1][di + 1] - c) / sc;
+        f[a * 11 + 8] = P->dx * fetch(S, 1, q, i, j) / sc;
+        f[a * 11 + 9] = P->dy * fetch(S, 2, q, i, j) / sc;
+        f[a * 11 + 10] = std::log10(range / (std::fabs(c) + 1e-30) + 1e-16) / 8.0;
+      }
+    }
+}
+
 // One 2D step restricted to a window of cells; out[field][comp][h][w].
 void orc_step2d_window(const orc_problem* P, const double* W, const double* V, const double* Y,
                        const double* Z, const uint8_t* flag, double t, double dt, int i0, int j0,

@@ -134,6 +134,11 @@ struct shweno_handle {
   int graph_steps = 0;
   // profiling: events around every kernel of every timed step
   bool timing = false;
+  // learned flag
+  bool learned = false;
+  float* net = nullptr;
+  uint8_t* raw_flags = nullptr;
+  float logit_thr = 0.f;
   std::vector<cudaEvent_t> tev;
   size_t tev_used = 0;
   int64_t timed_steps = 0;
@@ -157,7 +162,7 @@ shweno_status cuda_fail(shweno_handle* h, cudaError_t e, const char* where) {
   } while (0)
 
 int kernel_count(const shweno_handle* h) {
-  return h->P.dim == 1 ? shweno::kKernels1D : shweno::kKernels2D;
+  return h->P.dim == 1 ? shweno::kKernels1D : shweno::kKernels2D + (h->learned ? 1 : 0);
 }
 
 // Enqueues one step; with timing on, records events around each step kernel.
@@ -176,12 +181,19 @@ cudaError_t enqueue_step(shweno_handle* h) {
     ++h->timed_steps;
   }
   shweno::launch_begin_step(h->ctl, h->stream);
-  if (h->P.dim == 1)
+  if (h->P.dim == 1) {
     shweno::launch_step1d(h->P, h->ctl, h->buf[0], h->buf[1], h->buf[0], h->buf[1], h->flags,
                           h->FH, h->WE, h->stream, ev);
-  else
+  } else {
+    if (h->learned) {
+      if (ev) cudaEventRecord(ev[0], h->stream);
+      shweno::launch_infer2d(h->P, h->ctl, h->buf[0], h->buf[1], h->net, h->logit_thr, h->raw_flags,
+                             h->flags, h->stream);
+      if (ev) ++ev;
+    }
     shweno::launch_step2d(h->P, h->ctl, h->buf[0], h->buf[1], h->buf[0], h->buf[1], h->flags,
                           h->S, h->stream, ev);
+  }
   shweno::launch_end_step(h->ctl, h->stream);
   return cudaGetLastError();
 }
@@ -334,6 +346,8 @@ shweno_status shweno_destroy(shweno_handle* h) {
   for (int b = 0; b < 2; ++b) dev_free(h->buf[b]);
   dev_free(h->scratch);
   dev_free(h->flags);
+  dev_free(h->raw_flags);
+  dev_free(h->net);
   dev_free(h->ctl);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
   for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
@@ -552,7 +566,79 @@ const char* shweno_kernel_name(const shweno_handle* h, int k) {
   static const char* n1[] = {"face1d", "update1d"};
   static const char* n2[] = {"coef2d", "xface2d", "yface2d", "update2d"};
   if (!h || k < 0 || k >= kernel_count(h)) return "";
-  return h->P.dim == 1 ? n1[k] : n2[k];
+  if (h->P.dim == 1) return n1[k];
+  if (h->learned) return k == 0 ? "flags2d" : n2[k - 1];
+  return n2[k];
+}
+
+shweno_status shweno_flag_features(shweno_handle* h, float* out) {
+  if (!h || !out) return fail(h, SHWENO_E_INVALID, "null argument");
+  if (h->P.dim != 2 || h->P.eq != SHWENO_EULER) return fail(h, SHWENO_E_STATE, "features need a 2D Euler handle");
+  shweno::launch_features2d(h->P, h->ctl, h->buf[0], h->buf[1], out, h->stream);
+  CK(h, cudaGetLastError());
+  CK(h, cudaStreamSynchronize(h->stream));
+  return SHWENO_OK;
+}
+
+shweno_status shweno_weight_deviation(shweno_handle* h, double* out) {
+  if (!h || !out) return fail(h, SHWENO_E_INVALID, "null argument");
+  if (h->P.dim != 2 || h->P.eq != SHWENO_EULER) return fail(h, SHWENO_E_STATE, "needs a 2D Euler handle");
+  shweno::launch_wdev2d(h->P, h->ctl, h->buf[0], h->buf[1], out, h->stream);
+  CK(h, cudaGetLastError());
+  CK(h, cudaStreamSynchronize(h->stream));
+  return SHWENO_OK;
+}
+
+shweno_status shweno_mlp_forward(const float* params, const float* x, int64_t n, float* prob,
+                                 void* cuda_stream) {
+  if (!params || (n > 0 && (!x || !prob)) || n < 0) return SHWENO_E_INVALID;
+  shweno::mlp_forward(params, x, n, prob, (cudaStream_t)cuda_stream);
+  return cudaGetLastError() == cudaSuccess ? SHWENO_OK : SHWENO_E_CUDA;
+}
+
+shweno_status shweno_mlp_grad(const float* params, const float* x, const float* y, int64_t n,
+                              float pos_weight, float* grad, float* loss, void* cuda_stream) {
+  if (!params || !grad || !loss || n <= 0 || !x || !y) return SHWENO_E_INVALID;
+  return shweno::mlp_grad(params, x, y, n, pos_weight, grad, loss, (cudaStream_t)cuda_stream) == cudaSuccess
+             ? SHWENO_OK : SHWENO_E_CUDA;
+}
+
+shweno_status shweno_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t step,
+                              float lr, float beta1, float beta2, float eps, void* cuda_stream) {
+  if (!params || !grad || !m || !v || step < 1) return SHWENO_E_INVALID;
+  const float bc1 = (float)(1.0 - std::pow((double)beta1, (double)step));
+  const float bc2 = (float)(1.0 - std::pow((double)beta2, (double)step));
+  shweno::mlp_adam(params, grad, m, v, lr, beta1, beta2, eps, bc1, bc2, (cudaStream_t)cuda_stream);
+  return cudaGetLastError() == cudaSuccess ? SHWENO_OK : SHWENO_E_CUDA;
+}
+
+shweno_status shweno_set_flag_net(shweno_handle* h, const float* params, double threshold,
+                                  int on_device) {
+  if (!h || !params) return fail(h, SHWENO_E_INVALID, "null argument");
+  if (!(threshold > 0.0 && threshold < 1.0)) return fail(h, SHWENO_E_INVALID, "threshold must be in (0, 1)");
+  if (h->P.dim != 2 || h->P.eq != SHWENO_EULER || h->P.flag_mode != shweno::FLAG_PER_CELL)
+    return fail(h, SHWENO_E_STATE, "the learned flag needs a 2D Euler handle created with flag_mode 2");
+  if (!h->net) {
+    h->net = (float*)dev_alloc(SHWENO_FLAG_PARAMS * sizeof(float));
+    h->raw_flags = (uint8_t*)dev_alloc(h->cells);
+    if (!h->flags) h->flags = (uint8_t*)dev_alloc(h->cells);
+    if (!h->net || !h->raw_flags || !h->flags) return fail(h, SHWENO_E_NOMEM, "device allocation of the flag network failed");
+  }
+  CK(h, cudaMemcpyAsync(h->net, params, SHWENO_FLAG_PARAMS * sizeof(float),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  h->logit_thr = (float)std::log(threshold / (1.0 - threshold));
+  h->learned = true;
+  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; h->graph_steps = 0; }
+  return SHWENO_OK;
+}
+
+shweno_status shweno_get_flags(shweno_handle* h, uint8_t* out, int on_device) {
+  if (!h || !out) return fail(h, SHWENO_E_INVALID, "null argument");
+  if (!h->flags) return fail(h, SHWENO_E_STATE, "no flags yet");
+  CK(h, cudaMemcpyAsync(out, h->flags, h->cells, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return SHWENO_OK;
 }
 
 }  // extern "C"

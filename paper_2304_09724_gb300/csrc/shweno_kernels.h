@@ -31,6 +31,18 @@ void launch_step2d(const Params& P, Ctl* ctl, const double* s0, const double* s1
 size_t scratch2d_doubles(const Params& P);
 void init_kernels2d();  // kernel attributes (dynamic shared memory); call before any capture
 Scratch2D carve_scratch2d(const Params& P, double* base);
+void launch_features2d(const Params& P, const Ctl* ctl, const double* s0, const double* s1,
+                       float* out, cudaStream_t st);
+void launch_wdev2d(const Params& P, const Ctl* ctl, const double* s0, const double* s1,
+                   double* out, cudaStream_t st);
+void launch_infer2d(const Params& P, const Ctl* ctl, const double* s0, const double* s1,
+                    const float* params, float logit_thr, uint8_t* raw, uint8_t* flags,
+                    cudaStream_t st);
+void mlp_forward(const float* params, const float* X, int64_t n, float* prob, cudaStream_t st);
+cudaError_t mlp_grad(const float* params, const float* X, const float* y, int64_t n, float pw,
+                     float* grad, float* loss, cudaStream_t st);
+void mlp_adam(float* params, const float* grad, float* m, float* v, float lr, float b1, float b2,
+              float eps, float bc1, float bc2, cudaStream_t st);
 void launch_begin_step(Ctl* ctl, cudaStream_t st);
 void launch_end_step(Ctl* ctl, cudaStream_t st);
 void launch_rate(const Params& P, Ctl* ctl, const double* s0, const double* s1, cudaStream_t st);

@@ -1,0 +1,172 @@
+"""Training and evaluation driver of the learned troubled-cell flag.
+
+The network and its training step run in the library's own CUDA kernels (shweno_mlp_forward,
+shweno_mlp_grad, shweno_mlp_adam through the C ABI); PyTorch only holds the device buffers.
+Labels come from the plain scheme itself: seeded random four-quadrant Riemann problems (rho ~
+U[0.1,2], u, v ~ U[-1,1], p ~ U[0.1,2]) at 256 x 256 are advanced with the always-nonlinear
+scheme; at several snapshots every cell gets the features of shweno_flag_features and the label
+1 if shweno_weight_deviation exceeds delta (the nonlinear weights of some reconstruction anchored
+on the cell deviate from the linear ones by more than delta, relatively).
+
+    python -m paper_2304_09724_gb300.flagnet --out flagnet_weights.npz
+"""
+from __future__ import annotations
+
+import argparse
+import math
+import os
+import time
+
+import numpy as np
+
+from . import shweno as S
+from . import workloads as WL
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_WEIGHTS = os.path.join(HERE, "flagnet_weights.npz")
+NIN, NH = S.FLAG_FEATURES, 32
+
+
+def init_params(seed):
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0, math.sqrt(2 / NIN), (NH, NIN)), np.zeros(NH),
+             rng.normal(0, math.sqrt(2 / NH), (NH, NH)), np.zeros(NH),
+             rng.normal(0, math.sqrt(1 / NH), NH), np.zeros(1)]
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+def snapshot_data(seed, n=256, times=(0.0, 0.05, 0.1, 0.175, 0.25), delta=0.05):
+    """(features [k*cells][22], labels [k*cells], deviations) of one seeded problem (CUDA tensors).
+    A problem whose plain run leaves the physical range keeps the snapshots taken before."""
+    import torch
+
+    wl = WL.riemann2d(n, WL.random_quadrants(seed))
+    sol = S.Solver(2, S.EULER, n, n, wl.domain, wl.bc, flag_mode=0)
+    sol.set_state(wl.state)
+    X, D = [], []
+    for t in times:
+        if t > 0:
+            try:
+                sol.run(t, wl.cfl)
+            except S.ShwenoError as e:
+                if e.status != S.E_NONPHYSICAL:
+                    raise
+                break
+        x = torch.empty((n * n, NIN), dtype=torch.float32, device="cuda")
+        d = torch.empty(n * n, dtype=torch.float64, device="cuda")
+        S.shweno_flag_features(sol.h, x)
+        S.shweno_weight_deviation(sol.h, d)
+        X.append(x)
+        D.append(d)
+    sol.close()
+    X, D = torch.cat(X), torch.cat(D)
+    return X, (D > delta).float(), D
+
+
+def dataset(seeds, **kw):
+    import torch
+
+    parts = [snapshot_data(s, **kw) for s in seeds]
+    return torch.cat([p[0] for p in parts]), torch.cat([p[1] for p in parts])
+
+
+def train(X, y, epochs=6, batch=16384, lr=2e-3, seed=0, log=None):
+    """Adam on the weighted BCE with the library's kernels; returns the parameters (CUDA)."""
+    import torch
+
+    n = X.shape[0]
+    npos = float(y.sum().item())
+    pw = (n - npos) / max(npos, 1.0)
+    params = torch.from_numpy(init_params(seed)).cuda()
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    grad = torch.zeros_like(params)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    step = 0
+    for ep in range(epochs):
+        perm = torch.randperm(n, device="cuda", generator=gen)
+        tot = 0.0
+        for b0 in range(0, n, batch):
+            idx = perm[b0:b0 + batch]
+            xb, yb = X[idx].contiguous(), y[idx].contiguous()
+            S.shweno_mlp_grad(params, xb, yb, pw, grad, loss)
+            step += 1
+            S.shweno_mlp_adam(params, grad, m, v, step, lr)
+            tot += float(loss.item()) * xb.shape[0]
+        if log:
+            log(f"epoch {ep}: mean loss {tot / n:.4f}")
+    return params, pw
+
+
+def probabilities(params, X):
+    import torch
+
+    p = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+    S.shweno_mlp_forward(params, X, p)
+    return p
+
+
+def threshold_for_recall(params, X, y, recall=0.999):
+    """Largest threshold whose recall on (X, y) is at least `recall`."""
+    import torch
+
+    p = probabilities(params, X)
+    pos = torch.sort(p[y > 0.5]).values
+    if pos.numel() == 0:
+        return 0.5
+    k = int(math.floor((1.0 - recall) * pos.numel()))
+    thr = float(pos[k].item()) * (1.0 - 1e-6)
+    return min(max(thr, 1e-6), 1.0 - 1e-6)
+
+
+def evaluate(params, thr, X, y):
+    p = probabilities(params, X)
+    pred = p > thr
+    pos = y > 0.5
+    tp = float((pred & pos).sum().item())
+    return {"recall": tp / max(float(pos.sum().item()), 1.0), "flagged": float(pred.float().mean().item()),
+            "positives": float(pos.float().mean().item())}
+
+
+def save(path, params, thr, meta):
+    np.savez(path, params=params.cpu().numpy(), threshold=np.float64(thr), **{k: np.asarray(v) for k, v in meta.items()})
+
+
+def load(path=DEFAULT_WEIGHTS):
+    z = np.load(path)
+    return z["params"].astype(np.float32), float(z["threshold"])
+
+
+def main():
+    import torch
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=DEFAULT_WEIGHTS)
+    ap.add_argument("--train-seeds", type=int, default=12)
+    ap.add_argument("--val-seeds", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--recall", type=float, default=0.999)
+    args = ap.parse_args()
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    Xt, yt = dataset(range(100, 100 + args.train_seeds))
+    Xv, yv = dataset(range(500, 500 + args.val_seeds))
+    t1 = time.time()
+    params, pw = train(Xt, yt, epochs=args.epochs, log=print)
+    torch.cuda.synchronize()
+    t2 = time.time()
+    thr = threshold_for_recall(params, Xv, yv, args.recall)
+    ev_t, ev_v = evaluate(params, thr, Xt, yt), evaluate(params, thr, Xv, yv)
+    print(f"data {t1 - t0:.1f}s ({Xt.shape[0]} train / {Xv.shape[0]} val samples), train {t2 - t1:.1f}s, "
+          f"pos_weight {pw:.2f}, threshold {thr:.4g}")
+    print("train", ev_t)
+    print("val", ev_v)
+    save(args.out, params, thr, {"val_recall": ev_v["recall"], "val_flagged": ev_v["flagged"],
+                                 "val_positives": ev_v["positives"], "pos_weight": pw})
+    print("saved", args.out)
+
+
+if __name__ == "__main__":
+    main()

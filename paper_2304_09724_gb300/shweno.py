@@ -45,7 +45,10 @@ class ShwenoError(RuntimeError):
 EXPORTS = ["shweno_create", "shweno_set_state", "shweno_get_state", "shweno_step", "shweno_run",
            "shweno_advance", "shweno_sync", "shweno_set_timing", "shweno_get_timing",
            "shweno_kernel_name", "shweno_cfl_dt", "shweno_get_time", "shweno_set_flags",
-           "shweno_destroy", "shweno_last_error", "shweno_set_allocator", "shweno_step1d_noalloc"]
+           "shweno_destroy", "shweno_last_error", "shweno_set_allocator", "shweno_step1d_noalloc",
+           "shweno_flag_features", "shweno_weight_deviation", "shweno_mlp_forward", "shweno_mlp_grad",
+           "shweno_mlp_adam", "shweno_set_flag_net", "shweno_get_flags"]
+FLAG_FEATURES, FLAG_PARAMS = 22, 1825
 NOALLOC_MAX_NX = 65536
 
 _lib = None
@@ -82,6 +85,14 @@ def lib():
                                         ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_double * 4), ctypes.c_int32, vp, vp,
                                         ctypes.c_double, ctypes.c_double, vp]
+    L.shweno_flag_features.argtypes = [vp, vp]
+    L.shweno_weight_deviation.argtypes = [vp, vp]
+    L.shweno_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+    L.shweno_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_float, vp, vp, vp]
+    L.shweno_mlp_adam.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
+                                  ctypes.c_float, ctypes.c_float, vp]
+    L.shweno_set_flag_net.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int]
+    L.shweno_get_flags.argtypes = [vp, vp, ctypes.c_int]
     L.shweno_last_error.argtypes = [vp]
     L.shweno_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -188,6 +199,40 @@ def shweno_step1d_noalloc(eq, nx, x0, x1, gamma, bc, inflow, flag_mode, state_in
     infl = ((ctypes.c_double * 4) * 2)(*[(ctypes.c_double * 4)(*inflow[s]) for s in range(2)]) if inflow else None
     return lib().shweno_step1d_noalloc(eq, nx, x0, x1, gamma, kinds, infl, flag_mode, _ptr(state_in)[0],
                                        _ptr(state_out)[0], t, dt, stream or None)
+
+
+def shweno_flag_features(h, out):
+    """out: CUDA float32 tensor [cells][22]."""
+    _check(lib().shweno_flag_features(h, _ptr(out)[0]), h)
+
+
+def shweno_weight_deviation(h, out):
+    """out: CUDA float64 tensor [cells]."""
+    _check(lib().shweno_weight_deviation(h, _ptr(out)[0]), h)
+
+
+def shweno_mlp_forward(params, x, prob, stream=0):
+    _check(lib().shweno_mlp_forward(_ptr(params)[0], _ptr(x)[0], x.shape[0], _ptr(prob)[0], stream or None))
+
+
+def shweno_mlp_grad(params, x, y, pos_weight, grad, loss, stream=0):
+    _check(lib().shweno_mlp_grad(_ptr(params)[0], _ptr(x)[0], _ptr(y)[0], x.shape[0], pos_weight,
+                                 _ptr(grad)[0], _ptr(loss)[0], stream or None))
+
+
+def shweno_mlp_adam(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):
+    _check(lib().shweno_mlp_adam(_ptr(params)[0], _ptr(grad)[0], _ptr(m)[0], _ptr(v)[0], step, lr, beta1,
+                                 beta2, eps, stream or None))
+
+
+def shweno_set_flag_net(h, params, threshold):
+    p, dev = _ptr(params)
+    _check(lib().shweno_set_flag_net(h, p, threshold, dev), h)
+
+
+def shweno_get_flags(h, out):
+    p, dev = _ptr(out)
+    _check(lib().shweno_get_flags(h, p, dev), h)
 
 
 def shweno_destroy(h):
