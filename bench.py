@@ -143,6 +143,58 @@ def bench_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def measure_form(S, torch, wl, steps, warmup, flag_net=None):
+    """cell-updates/s of `steps` CFL steps (after `warmup`) of workload wl, plain or learned;
+    returns (rate, state after the steps, flagged fraction or None)."""
+    import numpy as np
+
+    stream = torch.cuda.Stream()
+    sol = S.Solver(2, S.EULER, wl.nx, wl.ny, wl.domain, wl.bc, inflow=wl.inflow,
+                   flag_mode=2 if flag_net else 0, stream=stream.cuda_stream)
+    dev = {k: torch.from_numpy(np.array(v)).cuda() for k, v in wl.state.items()}
+    torch.cuda.synchronize()
+    sol.set_state(dev)
+    if flag_net:
+        S.shweno_set_flag_net(sol.h, torch.from_numpy(flag_net[0]).cuda(), flag_net[1])
+    S.shweno_advance(sol.h, warmup, CFL)
+    S.shweno_sync(sol.h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    S.shweno_advance(sol.h, steps, CFL)
+    e1.record(stream)
+    S.shweno_sync(sol.h)
+    torch.cuda.synchronize()
+    rate = wl.nx * wl.ny * steps / (e0.elapsed_time(e1) / 1000.0)
+    st = sol.get_state()
+    frac = None
+    if flag_net:
+        flags = np.empty((wl.ny, wl.nx), dtype=np.uint8)
+        S.shweno_get_flags(sol.h, flags)
+        frac = float(flags.mean())
+    sol.close()
+    return rate, st, frac
+
+
+def learned_vs_plain(S, torch, WL, steps, warmup, vortex_wl):
+    """The learned-flag form against the always-nonlinear form on the vortex (the main workload)
+    and on the double Mach reflection at 4096 x 1024 (the learned flag's workload): rates, the
+    flagged fraction and the relative L1 deviation of W after the same steps."""
+    import numpy as np
+
+    from paper_2304_09724_gb300 import flagnet as F
+
+    net = F.load()
+    out = {}
+    for name, wl in (("isentropic_vortex_%dx%d" % (vortex_wl.nx, vortex_wl.ny), vortex_wl),
+                     ("double_mach_reflection_4096x1024", WL.dmr(4096, 1024))):
+        rp, sp, _ = measure_form(S, torch, wl, steps, warmup)
+        rl, sl, frac = measure_form(S, torch, wl, steps, warmup, flag_net=net)
+        dev = float(np.sum(np.abs(sl["W"] - sp["W"])) / np.sum(np.abs(sp["W"])))
+        out[name] = {"plain": rp, "learned": rl, "speedup": rl / rp, "flagged_fraction": frac,
+                     "rel_l1_vs_plain_after_steps": dev, "steps": steps}
+    return out
+
+
 def bench_gpu(args):
     import numpy as np
     import torch
@@ -253,6 +305,8 @@ def bench_gpu(args):
                 "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
         "gpu_launches": 3 + 6 * args.steps,
     }
+    if not args.no_learned:
+        line["learned_flag"] = learned_vs_plain(S, torch, WL, args.steps, args.warmup, wl)
     if not args.no_cpu_baseline:
         rate, el = oracle_sample(wl, args.cpu_window, 1)
         line["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
@@ -270,6 +324,7 @@ def main():
     ap.add_argument("--cpu-window", type=int, default=160)
     ap.add_argument("--ref-window", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)

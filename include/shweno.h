@@ -207,6 +207,41 @@ shweno_status shweno_set_flag_net(shweno_handle* h, const float* params, double 
 /* Flags used by the last step (after dilation), [ny][nx] bytes. */
 shweno_status shweno_get_flags(shweno_handle* h, uint8_t* out, int on_device);
 
+/* ---------------------------------------------------------------- batched persistent launch
+ * Not in the paper: many independent problems (existing handles, 1D and 2D mixed, uneven sizes,
+ * each with its own CFL time step and end time) advanced together by one persistent kernel,
+ * launched from a CUDA graph.  Work items (problem, phase, index) flow through a device queue;
+ * the CTA that finishes a problem's last item of a phase enqueues the next phase or commits the
+ * step on the problem's own control block, so every handle stays usable on its own afterwards.
+ * The only device-side wait is for an empty queue; it is bounded (about a second by default,
+ * shweno_batch_set), after which the run returns SHWENO_E_TIMEOUT.  The handles must outlive
+ * the batch and must not be used on their own while a batch run is in flight. */
+typedef struct shweno_batch shweno_batch;
+
+/* Groups n handles.  cuda_stream: stream of the batch's work (NULL: its own). */
+shweno_status shweno_batch_create(shweno_handle* const* hs, int n, void* cuda_stream,
+                                  shweno_batch** out);
+
+/* Advances every problem p to t_final[p] (host array) with dt = cfl / rate, or by at most
+ * max_steps steps when max_steps > 0.  per_problem (may be NULL) receives each problem's status
+ * (OK, NONPHYSICAL: stopped at its last good state, TIMEOUT).  Returns TIMEOUT if a device-side
+ * wait ran out, CUDA on a CUDA error, otherwise OK (even if some problems are NONPHYSICAL). */
+shweno_status shweno_batch_run(shweno_batch* b, const double* t_final, double cfl, int64_t max_steps,
+                               shweno_status* per_problem);
+
+/* Autotuner: times the candidate launch shapes (1D tile of 128..1024 cells, 1 or 2 CTAs per SM)
+ * on trial_steps steps of the actual problems, restoring every state afterwards, and keeps the
+ * fastest; the choice is written to tile1d_out / ctas_per_sm_out (may be NULL). */
+shweno_status shweno_batch_autotune(shweno_batch* b, const double* t_final, double cfl,
+                                    int64_t trial_steps, int* tile1d_out, int* ctas_per_sm_out);
+
+/* Sets the launch shape by hand and the bound of the empty-queue wait (values <= 0 keep the
+ * current setting).  tile1d: power of 2 in [128, 1024]; ctas_per_sm: 1 or 2. */
+shweno_status shweno_batch_set(shweno_batch* b, int tile1d, int ctas_per_sm, int64_t spin_limit);
+
+shweno_status shweno_batch_destroy(shweno_batch* b);
+const char* shweno_batch_last_error(const shweno_batch* b);
+
 /* Allocation-free single 1D step.  The paper has no counterpart: this is a convenience for
  * callers that cannot allocate device memory when they step -- code running inside an open
  * CUDA stream capture (allocation is not capturable and synchronises the device), real-time

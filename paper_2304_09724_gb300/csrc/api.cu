@@ -232,6 +232,25 @@ bool valid_bc(int k, int dim, int side) {
 
 }  // namespace
 
+namespace shweno {
+bool handle_view(shweno_handle* h, HandleView* v) {
+  if (!h || !v) return false;
+  v->P = h->P;
+  v->ctl = h->ctl;
+  v->buf[0] = h->buf[0];
+  v->buf[1] = h->buf[1];
+  v->flags = h->flags;
+  v->S = h->S;
+  v->net = h->net;
+  v->raw = h->raw_flags;
+  v->flags_out = h->flags;
+  v->logit_thr = h->logit_thr;
+  v->learned = h->learned ? 1 : 0;
+  v->stream = h->stream;
+  return true;
+}
+}  // namespace shweno
+
 extern "C" {
 
 shweno_status shweno_set_allocator(shweno_alloc_fn alloc, shweno_free_fn release, void* ctx) {
@@ -295,7 +314,7 @@ shweno_status shweno_create(const shweno_grid* grid, double gamma, const shweno_
   P.eps = o.eps;
   for (int k = 0; k < 3; ++k) P.gam[k] = o.gam[k];
   P.flag_mode = o.flag_mode;
-  shweno::set_ck_factors(P);
+  shweno::finalize_params(P);
 
   h->cells = (size_t)P.nx * P.ny;
   h->nfields = dim == 2 ? 4 : 2;

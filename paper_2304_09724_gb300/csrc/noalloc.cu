@@ -116,6 +116,7 @@ extern "C" shweno_status shweno_step1d_noalloc(int32_t eq, int64_t nx, double x0
   P.gam[1] = 0.003;
   P.gam[2] = 0.003;
   P.flag_mode = flag_mode;
+  shweno::finalize_params(P);
 
   cudaStream_t st = (cudaStream_t)cuda_stream;
   noalloc_begin_kernel<<<1, 1, 0, st>>>(ctl, t, dt);

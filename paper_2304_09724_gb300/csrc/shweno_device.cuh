@@ -29,15 +29,17 @@ struct Params {
   int32_t flag_mode;      // FLAG_*
   // Cauchy-Kovalevskaya scale factors (m+1)/((k+1) dx) and (n+1)/((k+1) dy), set by the host
   double ckx[5][4], cky[5][4];
+  double igam[3];  // 1 / gam, set by the host
 };
 
-// Fills Params::ckx / cky from dx, dy.
-inline void set_ck_factors(Params& P) {
+// Fills the derived members of Params (ckx, cky, igam) from dx, dy and gam.
+inline void finalize_params(Params& P) {
   for (int m = 0; m < 5; ++m)
     for (int k = 0; k < 4; ++k) {
       P.ckx[m][k] = (m + 1) / ((k + 1) * P.dx);
       P.cky[m][k] = (m + 1) / ((k + 1) * P.dy);
     }
+  for (int l = 0; l < 3; ++l) P.igam[l] = 1.0 / P.gam[l];
 }
 
 // Device-resident time-stepping control block.  One step = begin_step, the step kernels,
@@ -55,6 +57,23 @@ struct Ctl {
   int32_t err;                 // first error code seen (ERR_*), sticky
   int32_t pad;
 };
+
+// Snapshot of the step in flight, read with volatile loads: inside the batched persistent
+// kernel the control block is rewritten by other CTAs between steps, so an L1-cached copy
+// could be stale.
+struct StepView {
+  int odd;    // committed state is buffer 1 (else 0)
+  double t;   // time of the committed state
+  double dt;  // step being taken
+};
+__device__ __forceinline__ StepView step_view(const Ctl* c) {
+  const volatile Ctl* v = c;
+  StepView s;
+  s.odd = (int)(v->nsteps & 1);
+  s.t = v->t;
+  s.dt = v->dt;
+  return s;
+}
 
 // ------------------------------------------------------------------ boundary conditions
 // Ghost cells are never stored: every load maps its (i, j) onto the interior, or onto an imposed
@@ -123,13 +142,15 @@ __device__ __forceinline__ Mapped map_cell(const Params& P, int f, int q, int i,
 }
 
 // Loads field f, component q of cell (i, j) (any i, j) from a state laid out [f][q][ny][nx].
+// Loads go through L2 only (ld.global.cg): the batched persistent kernel reads states that other
+// SMs wrote earlier in the same launch.
 __device__ __forceinline__ double fetch(const Params& P, const double* __restrict__ state, int f,
                                         int q, int i, int j, double t) {
   if (i >= 0 && i < P.nx && (P.dim == 1 || (j >= 0 && j < P.ny)))
-    return __ldg(state + (((size_t)f * P.ncomp + q) * P.ny + j) * P.nx + i);
+    return __ldcg(state + (((size_t)f * P.ncomp + q) * P.ny + j) * P.nx + i);
   const Mapped m = map_cell(P, f, q, i, j, t);
   if (m.fixed) return m.value;
-  return m.sign * __ldg(state + (((size_t)f * P.ncomp + q) * P.ny + m.j) * P.nx + m.i);
+  return m.sign * __ldcg(state + (((size_t)f * P.ncomp + q) * P.ny + m.j) * P.nx + m.i);
 }
 
 // Flag of the cell a reconstruction is anchored on (1 = nonlinear weights).  Ghost cells take
@@ -152,7 +173,7 @@ __device__ __forceinline__ int cell_flag(const Params& P, const uint8_t* __restr
     else if (k == BC_REFLECTIVE) j = j < 0 ? -1 - j : 2 * P.ny - 1 - j;
     else return 1;
   }
-  return flag[(size_t)j * P.nx + i] ? 1 : 0;
+  return __ldcg(flag + (size_t)j * P.nx + i) ? 1 : 0;
 }
 
 // ------------------------------------------------------------------ SHWENO reconstruction
@@ -186,11 +207,14 @@ __device__ __forceinline__ Mix shweno_mix(const Params& P, double Wm, double W0,
   const double b2 = d2 * d2, b3 = d3 * d3;
   double tau = 0.5 * (fabs(b1 - b2) + fabs(b1 - b3));
   tau = tau * tau;
-  const double w1 = P.gam[0] * (1.0 + tau / (b1 + P.eps));
-  const double w2 = P.gam[1] * (1.0 + tau / (b2 + P.eps));
-  const double w3 = P.gam[2] * (1.0 + tau / (b3 + P.eps));
+  // the three 1/(b_l + eps) from one division
+  const double e1 = b1 + P.eps, e2 = b2 + P.eps, e3 = b3 + P.eps;
+  const double e12 = e1 * e2, r = 1.0 / (e12 * e3);
+  const double w1 = P.gam[0] * (1.0 + tau * (e2 * e3 * r));
+  const double w2 = P.gam[1] * (1.0 + tau * (e1 * e3 * r));
+  const double w3 = P.gam[2] * (1.0 + tau * (e12 * r));
   const double inv = 1.0 / (w1 + w2 + w3);
-  const double A = w1 * inv / P.gam[0];
+  const double A = w1 * inv * P.igam[0];
   return Mix{A, w2 * inv - A * P.gam[1], w3 * inv - A * P.gam[2]};
 }
 
@@ -372,6 +396,8 @@ struct Upwinder {
     for (int k = 0; k < NC; ++k) {
       const double H = lam[k] > tol ? 1.0 : (lam[k] < -tol ? 0.0 : 0.5);
       s[k] = base_left ? H - 1.0 : H;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) l[k][q] *= s[k];  // apply() then needs no extra product
     }
   }
 
@@ -388,13 +414,24 @@ struct Upwinder {
         double a = 0.0;
 #pragma unroll
         for (int q = 0; q < NC; ++q) a += l[k][q] * d[q];
-        a *= s[k];
 #pragma unroll
         for (int q = 0; q < NC; ++q) out[q] += a * r[k][q];
       }
     }
   }
 };
+
+// Normalised Taylor coefficients e[m] of the polynomial sum C[k] xi^k about xi0, m <= mmax
+// (repeated synthetic division).
+__device__ __forceinline__ void taylor_shift(double e[5], double xi0, int mmax) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (i > mmax) break;
+#pragma unroll
+    for (int k = 3; k >= 0; --k)
+      if (k >= i) e[k] += xi0 * e[k + 1];
+  }
+}
 
 // Max characteristic rate of one cell for the CFL step size: (|u|+c)/dx (+ (|v|+c)/dy).
 __device__ __forceinline__ double cell_rate(const Params& P, const double* W) {

@@ -43,6 +43,20 @@ cudaError_t mlp_grad(const float* params, const float* X, const float* y, int64_
                      float* grad, float* loss, cudaStream_t st);
 void mlp_adam(float* params, const float* grad, float* m, float* v, float lr, float b1, float b2,
               float eps, float bc1, float bc2, cudaStream_t st);
+// What the batch needs to know about a handle (filled by api.cu).
+struct HandleView {
+  Params P;
+  Ctl* ctl;
+  double* buf[2];
+  const uint8_t* flags;
+  Scratch2D S;
+  const float* net;
+  uint8_t* raw;
+  uint8_t* flags_out;
+  float logit_thr;
+  int learned;
+  cudaStream_t stream;
+};
 void launch_begin_step(Ctl* ctl, cudaStream_t st);
 void launch_end_step(Ctl* ctl, cudaStream_t st);
 void launch_rate(const Params& P, Ctl* ctl, const double* s0, const double* s1, cudaStream_t st);

@@ -18,27 +18,13 @@
 //   update2d one thread per cell: Eq. (3.2) and Eq. (3.10), physical check, CFL rate.
 #include <cuda_runtime.h>
 
-#include "ck_generated.cuh"
-#include "shweno_device.cuh"
 #include "shweno_kernels.h"
+#include "step2d_items.cuh"
 
 namespace shweno {
 
-constexpr int SEG = 128;       // face points per CTA
-constexpr int SPAN = SEG + 3;  // first-pass evaluations a CTA needs
-constexpr int TX = 32, TY = 8; // coef2d tile
+constexpr int TY = 8;  // coef2d tile height of the one-mesh kernel
 
-__device__ __forceinline__ void taylor_shift2(double e[5], double xi0, int mmax) {
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    if (i > mmax) break;
-#pragma unroll
-    for (int k = 3; k >= 0; --k)
-      if (k >= i) e[k] += xi0 * e[k + 1];
-  }
-}
-
-// ------------------------------------------------------------------ first pass
 __global__ void __launch_bounds__(TX * TY) coef2d_kernel(Params P, const Ctl* __restrict__ ctl,
                                                          const double* s0, const double* s1,
                                                          const uint8_t* __restrict__ flag,
@@ -46,198 +32,11 @@ __global__ void __launch_bounds__(TX * TY) coef2d_kernel(Params P, const Ctl* __
                                                          double* __restrict__ xcoef) {
   __shared__ double tile[16][TY + 2][TX + 2];
   if (!ctl->active) return;
-  const double* st = (ctl->nsteps & 1) ? s1 : s0;
-  const double t = ctl->t;
-  const int bx = blockIdx.x * TX - 2, by = blockIdx.y * TY - 2;
-  const int tid = threadIdx.y * TX + threadIdx.x;
-  for (int idx = tid; idx < 16 * (TY + 2) * (TX + 2); idx += TX * TY) {
-    const int xx = idx % (TX + 2), rest = idx / (TX + 2);
-    const int yy = rest % (TY + 2), fq = rest / (TY + 2);
-    const int i = bx - 1 + xx, j = by - 1 + yy;
-    double v = 0.0;
-    if (i >= -3 && i <= P.nx + 2 && j >= -3 && j <= P.ny + 2) v = fetch(P, st, fq >> 2, fq & 3, i, j, t);
-    tile[fq][yy][xx] = v;
-  }
-  __syncthreads();
-  const int ic = bx + threadIdx.x, jr = by + threadIdx.y;
-  const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
-  const int NX4 = P.nx + 4, NY2 = P.ny + 2, NY4 = P.ny + 4;
-  if (ic <= P.nx + 1 && jr >= -1 && jr <= P.ny) {  // y-pass: {W,Y} and {V,Z} along a column
-    const int nl = cell_flag(P, flag, ic, jr);
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int fa = (s == 0 ? 0 : 1) * 4 + q, fd = (s == 0 ? 2 : 3) * 4 + q;
-        const double Wm = tile[fa][ly - 1][lx], W0 = tile[fa][ly][lx], Wp = tile[fa][ly + 1][lx];
-        const double vm = P.dy * tile[fd][ly - 1][lx], vp = P.dy * tile[fd][ly + 1][lx];
-        double c[5], C[5];
-        p1_coeffs(Wm, W0, Wp, vm, vp, c);
-        mix_coeffs(shweno_mix(P, Wm, W0, Wp, c, nl), Wm, W0, Wp, c, C);
-        const double sc = s == 0 ? 1.0 : P.dx;  // x-pass derivative data: dx * avg(W_x)
-#pragma unroll
-        for (int k = 0; k < 5; ++k)
-          ycoef[((size_t)((s * 4 + q) * 5 + k) * NY2 + (jr + 1)) * NX4 + (ic + 2)] = sc * C[k];
-      }
-  }
-  if (ic >= 0 && ic < P.nx && jr <= P.ny + 1) {  // x-pass: {W,V} and {Y,Z} along a row
-    const int nl = cell_flag(P, flag, ic, jr);
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int fa = (s == 0 ? 0 : 2) * 4 + q, fd = (s == 0 ? 1 : 3) * 4 + q;
-        const double Wm = tile[fa][ly][lx - 1], W0 = tile[fa][ly][lx], Wp = tile[fa][ly][lx + 1];
-        const double vm = P.dx * tile[fd][ly][lx - 1], vp = P.dx * tile[fd][ly][lx + 1];
-        double c[5], C[5];
-        p1_coeffs(Wm, W0, Wp, vm, vp, c);
-        mix_coeffs(shweno_mix(P, Wm, W0, Wp, c, nl), Wm, W0, Wp, c, C);
-        const double sc = s == 0 ? 1.0 : P.dy;  // y-pass derivative data: dy * avg(W_y)
-#pragma unroll
-        for (int k = 0; k < 5; ++k)
-          xcoef[((size_t)((s * 4 + q) * 5 + k) * P.nx + ic) * NY4 + (jr + 2)] = sc * C[k];
-      }
-  }
+  coef2d_item<TY>(P, step_view(ctl), s0, s1, flag, ycoef, xcoef, blockIdx.x * TX - 2, blockIdx.y * TY - 2, tile,
+                  threadIdx.x, threadIdx.y);
 }
 
-// ------------------------------------------------------------------ one face point
-// Second pass across the face.  ev[set*4+q][k][col] holds the first-pass Taylor coefficients
-// (order k along the face) of a row of stencil columns.  Each cell's weights come from its
-// order-0 data and serve every order (remark ending Section 2.1.2) and both of the cell's faces:
-// they are computed once per cell (cell_mixes) into shared memory.
-struct MixTable {
-  double A[4][SPAN], B[4][SPAN], C[4][SPAN];  // p = A p1 + B p2 + C p3 per (comp, cell column)
-};
-
-constexpr size_t kEvBytes = sizeof(double) * 8 * 5 * SPAN;
-constexpr size_t kFaceSmem = kEvBytes + sizeof(MixTable);
-
-// Weights of the cells in columns 1..SEG+1 (the cells whose faces the CTA owns).  nl(col)
-// returns whether the cell of column col uses the nonlinear weights.
-template <typename FlagOf>
-__device__ __forceinline__ void cell_mixes(const Params& P, const double (*ev)[5][SPAN],
-                                           MixTable& mt, FlagOf nl) {
-  for (int it = threadIdx.x; it < 4 * (SEG + 1); it += SEG) {
-    const int q = it / (SEG + 1), c = 1 + it % (SEG + 1);
-    const double Wm = ev[q][0][c - 1], W0 = ev[q][0][c], Wp = ev[q][0][c + 1];
-    double cf[5];
-    p1_coeffs(Wm, W0, Wp, ev[4 + q][0][c - 1], ev[4 + q][0][c + 1], cf);
-    const Mix m = shweno_mix(P, Wm, W0, Wp, cf, nl(c));
-    mt.A[q][c] = m.A;
-    mt.B[q][c] = m.B;
-    mt.C[q][c] = m.C;
-  }
-}
-
-// Cross-face Taylor coefficients e[p] (p <= 4 - k) of tangential order k, component q, of the
-// cell in column c0 + 1 (stencil c0..c0+2), at its right end (PLUS, xi = +1/2) or left end:
-//   e[p] = A * END[p] . data + (small-stencil terms for p <= 1),
-// with END the constant rows of p1's Taylor coefficients at the end and data = (W-, W0, W+,
-// v-, v+) of order k.
-template <bool PLUS>
-__device__ __forceinline__ void side_out(const double (*ev)[5][SPAN], int c0, int q, int k, double A,
-                                         double B, double C, double e[5]) {
-  using namespace shweno_tables;
-  const double d[5] = {ev[q][k][c0], ev[q][k][c0 + 1], ev[q][k][c0 + 2], ev[4 + q][k][c0],
-                       ev[4 + q][k][c0 + 2]};
-#pragma unroll
-  for (int p = 0; p + k <= 4; ++p) e[p] = A * end_dot<PLUS>(p, d);
-  // p2 = W0 + (W0 - W-) xi and p3 = W0 + (W+ - W0) xi: value and slope at the end
-  if (PLUS) e[0] += (1.5 * B + 0.5 * C) * d[1] - 0.5 * B * d[0] + 0.5 * C * d[2];
-  else e[0] += (0.5 * B + 1.5 * C) * d[1] + 0.5 * B * d[0] - 0.5 * C * d[2];
-  if (k <= 3) e[1] += (B - C) * d[1] - B * d[0] + C * d[2];
-}
-
-// Face point: both sides' second pass, HLLC, upwinding, CK; returns the time-Taylor
-// coefficients tc[q][0..4].  Left cell in column c0 + 1, right cell in c0 + 2.  dir = 0: x-face
-// (first pass along y), 1: y-face.
-__device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5][SPAN],
-                                           const MixTable& mt, int c0, int dir, double tc[4][5]) {
-  const double g = P.gamma;
-  double a[4][25];
-  double dl[4][5], dr[4][5];
-  double AL[4], BL[4], CL[4], AR[4], BR[4], CR[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    AL[q] = mt.A[q][c0 + 1]; BL[q] = mt.B[q][c0 + 1]; CL[q] = mt.C[q][c0 + 1];
-    AR[q] = mt.A[q][c0 + 2]; BR[q] = mt.B[q][c0 + 2]; CR[q] = mt.C[q][c0 + 2];
-  }
-  // tangential order 0 first: it carries the leading-term data
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    side_out<true>(ev, c0, q, 0, AL[q], BL[q], CL[q], dl[q]);
-    side_out<false>(ev, c0 + 1, q, 0, AR[q], BR[q], CR[q], dr[q]);
-  }
-  double WL[4], WR[4], Ws[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) { WL[q] = dl[q][0]; WR[q] = dr[q][0]; }
-  hllc_state<4>(WL, WR, g, dir, Ws);
-  Upwinder<4> U;
-  U.setup(Ws, g, dir);
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    if (k > 0) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        side_out<true>(ev, c0, q, k, AL[q], BL[q], CL[q], dl[q]);
-        side_out<false>(ev, c0 + 1, q, k, AR[q], BR[q], CR[q], dr[q]);
-      }
-    }
-#pragma unroll
-    for (int p = 0; p + k <= 4; ++p) {
-      if (p == 0 && k == 0) continue;
-      double x[4], y[4], o[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) { x[q] = dl[q][p]; y[q] = dr[q][p]; }
-      U.apply(x, y, o);
-      // p is the order across the face, k the order along it
-      const int idx = dir == 0 ? p * 5 + k : k * 5 + p;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) a[q][idx] = o[q];
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) a[q][0] = Ws[q];
-  double t4[4][5];
-  ck_euler2d(a, t4, P.ckx, P.cky, g - 1.0);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    tc[q][0] = Ws[q];
-#pragma unroll
-    for (int k = 1; k < 5; ++k) tc[q][k] = t4[q][k];
-  }
-}
-
-// Lobatto time average of the flux along dir and the state at tau = dt.
-__device__ __forceinline__ void lobatto(const double tc[4][5], double dt, double g, int dir,
-                                        double Fh[4], double We[4]) {
-  using namespace shweno_tables;
-  const double taus[4] = {0.0, LOB_L1 * dt, LOB_L2 * dt, dt};
-  const double wts[4] = {LOB_W0, LOB_W1, LOB_W1, LOB_W0};
-#pragma unroll
-  for (int q = 0; q < 4; ++q) Fh[q] = 0.0;
-#pragma unroll
-  for (int al = 0; al < 4; ++al) {
-    double W[4], F[4];
-    const double tau = taus[al];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      W[q] = (((tc[q][4] * tau + tc[q][3]) * tau + tc[q][2]) * tau + tc[q][1]) * tau + tc[q][0];
-    phys_flux<4>(W, g, dir, F);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) Fh[q] += wts[al] * F[q];
-    if (al == 3) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) We[q] = W[q];
-    }
-  }
-}
-
-__device__ __forceinline__ double state_at(const double tc[5], double tau) {
-  return (((tc[4] * tau + tc[3]) * tau + tc[2]) * tau + tc[1]) * tau + tc[0];
-}
-
-// ------------------------------------------------------------------ x-faces and corners
+template <bool FLAGS>
 __global__ void __launch_bounds__(SEG) xface2d_kernel(Params P, const Ctl* __restrict__ ctl,
                                                       const double* __restrict__ ycoef,
                                                       const uint8_t* __restrict__ flag,
@@ -245,113 +44,24 @@ __global__ void __launch_bounds__(SEG) xface2d_kernel(Params P, const Ctl* __res
                                                       double* __restrict__ WX,
                                                       double* __restrict__ WC) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double(*ev)[5][SPAN] = reinterpret_cast<double(*)[5][SPAN]>(smem_raw);
-  MixTable& mt = *reinterpret_cast<MixTable*>(smem_raw + kEvBytes);
   if (!ctl->active) return;
   const int slice = blockIdx.z;  // 0..2: Gauss point of the rows; 3: corner rows
   const int row = blockIdx.y;    // Gauss: cell row j; corner: corner row jc (y_{jc-1/2})
   if (slice < 3 && row >= P.ny) return;
-  const int f0 = blockIdx.x * SEG;
-  const int NX4 = P.nx + 4, NY2 = P.ny + 2;
-  using namespace shweno_tables;
-  for (int it = threadIdx.x; it < 8 * SPAN; it += SEG) {
-    const int col = it % SPAN, rq = it / SPAN;
-    const int tcol = f0 + col;
-    double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    if (tcol >= NX4) {
-    } else if (slice < 3) {
-      const double* src = ycoef + ((size_t)(rq * 5) * NY2 + (row + 1)) * NX4 + tcol;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) e[k] = src[(size_t)k * NY2 * NX4];
-      if (slice != 1) taylor_shift2(e, slice == 0 ? -GAUSS_G : GAUSS_G, 4);
-    } else {
-      double lo[5], hi[5];
-      const double* slo = ycoef + ((size_t)(rq * 5) * NY2 + row) * NX4 + tcol;
-      const double* shi = slo + NX4;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) { lo[k] = slo[(size_t)k * NY2 * NX4]; hi[k] = shi[(size_t)k * NY2 * NX4]; }
-      taylor_shift2(lo, 0.5, 4);
-      taylor_shift2(hi, -0.5, 4);
-#pragma unroll
-      for (int k = 0; k < 5; ++k) e[k] = 0.5 * (lo[k] + hi[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < 5; ++k) ev[rq][k][col] = e[k];
-  }
-  __syncthreads();
-  // cell column c holds cell i = f0 + c - 2; a corner row uses the rows below and above
-  cell_mixes(P, ev, mt, [&](int c) {
-    const int i = f0 + c - 2;
-    return slice < 3 ? cell_flag(P, flag, i, row)
-                     : (cell_flag(P, flag, i, row - 1) | cell_flag(P, flag, i, row));
-  });
-  __syncthreads();
-  const int fi = f0 + threadIdx.x;  // face x_{fi-1/2}
-  if (fi > P.nx) return;
-  double tc[4][5];
-  face_point(P, ev, mt, threadIdx.x, 0, tc);
-  const double dt = ctl->dt;
-  if (slice < 3) {
-    double Fh[4], We[4];
-    lobatto(tc, dt, P.gamma, 0, Fh, We);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const size_t o = ((size_t)(slice * 4 + q) * P.ny + row) * (P.nx + 1) + fi;
-      FX[o] = Fh[q];
-      WX[o] = We[q];
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) WC[((size_t)q * (P.ny + 1) + row) * (P.nx + 1) + fi] = state_at(tc[q], dt);
-  }
+  xface_item<FLAGS>(P, step_view(ctl), ycoef, flag, FX, WX, WC, blockIdx.x * SEG, row, slice, smem_raw);
 }
 
-// ------------------------------------------------------------------ y-faces
+template <bool FLAGS>
 __global__ void __launch_bounds__(SEG) yface2d_kernel(Params P, const Ctl* __restrict__ ctl,
                                                       const double* __restrict__ xcoef,
                                                       const uint8_t* __restrict__ flag,
                                                       double* __restrict__ FY,
                                                       double* __restrict__ WY) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double(*ev)[5][SPAN] = reinterpret_cast<double(*)[5][SPAN]>(smem_raw);
-  MixTable& mt = *reinterpret_cast<MixTable*>(smem_raw + kEvBytes);
   if (!ctl->active) return;
-  const int slice = blockIdx.z;  // Gauss point of the columns
-  const int col = blockIdx.y;    // cell column i
-  const int f0 = blockIdx.x * SEG;
-  const int NY4 = P.ny + 4;
-  using namespace shweno_tables;
-  for (int it = threadIdx.x; it < 8 * SPAN; it += SEG) {
-    const int r = it % SPAN, rq = it / SPAN;
-    const int trow = f0 + r;
-    double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    if (trow < NY4) {
-      const double* src = xcoef + ((size_t)(rq * 5) * P.nx + col) * NY4 + trow;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) e[k] = src[(size_t)k * P.nx * NY4];
-      if (slice != 1) taylor_shift2(e, slice == 0 ? -GAUSS_G : GAUSS_G, 4);
-    }
-#pragma unroll
-    for (int k = 0; k < 5; ++k) ev[rq][k][r] = e[k];
-  }
-  __syncthreads();
-  cell_mixes(P, ev, mt, [&](int c) { return cell_flag(P, flag, col, f0 + c - 2); });
-  __syncthreads();
-  const int fj = f0 + threadIdx.x;  // face y_{fj-1/2}
-  if (fj > P.ny) return;
-  double tc[4][5];
-  face_point(P, ev, mt, threadIdx.x, 1, tc);
-  double Gh[4], We[4];
-  lobatto(tc, ctl->dt, P.gamma, 1, Gh, We);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const size_t o = ((size_t)(slice * 4 + q) * (P.ny + 1) + fj) * P.nx + col;
-    FY[o] = Gh[q];
-    WY[o] = We[q];
-  }
+  yface_item<FLAGS>(P, step_view(ctl), xcoef, flag, FY, WY, blockIdx.x * SEG, blockIdx.y, blockIdx.z, smem_raw);
 }
 
-// ------------------------------------------------------------------ update
 __global__ void __launch_bounds__(256) update2d_kernel(Params P, Ctl* __restrict__ ctl,
                                                        const double* s0, const double* s1,
                                                        double* o0, double* o1,
@@ -363,44 +73,9 @@ __global__ void __launch_bounds__(256) update2d_kernel(Params P, Ctl* __restrict
   __shared__ double red[32];
   if (!ctl->active) return;
   const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
-  const bool odd = ctl->nsteps & 1;
-  const double* st = odd ? s1 : s0;
-  double* out = odd ? o0 : o1;
-  const double dt = ctl->dt;
-  const int nx = P.nx, ny = P.ny;
-  using namespace shweno_tables;
-  const double gw[3] = {GAUSS_W0, GAUSS_W1, GAUSS_W0};
+  const StepView sv = step_view(ctl);
   double rate = 0.0;
-  if (i < nx && j < ny) {
-    double Wn[4];
-    const size_t cells = (size_t)nx * ny, c = (size_t)j * nx + i;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      double fl = 0.0, fr = 0.0, gb = 0.0, gt = 0.0, wl = 0.0, wr = 0.0, wb = 0.0, wt = 0.0;
-#pragma unroll
-      for (int g = 0; g < 3; ++g) {
-        const size_t ox = ((size_t)(g * 4 + q) * ny + j) * (nx + 1) + i;
-        const size_t oy = ((size_t)(g * 4 + q) * (ny + 1) + j) * nx + i;
-        fl += gw[g] * FX[ox];
-        fr += gw[g] * FX[ox + 1];
-        wl += gw[g] * WX[ox];
-        wr += gw[g] * WX[ox + 1];
-        gb += gw[g] * FY[oy];
-        gt += gw[g] * FY[oy + nx];
-        wb += gw[g] * WY[oy];
-        wt += gw[g] * WY[oy + nx];
-      }
-      const size_t oc = ((size_t)q * (ny + 1) + j) * (nx + 1) + i;
-      const double z = (WC[oc + (nx + 1) + 1] - WC[oc + (nx + 1)] - WC[oc + 1] + WC[oc]) / (P.dx * P.dy);
-      Wn[q] = st[q * cells + c] - dt / P.dx * (fr - fl) - dt / P.dy * (gt - gb);
-      out[q * cells + c] = Wn[q];
-      out[(4 + q) * cells + c] = (wr - wl) / P.dx;
-      out[(8 + q) * cells + c] = (wt - wb) / P.dy;
-      out[(12 + q) * cells + c] = z;
-    }
-    if (!cell_physical(P, Wn)) atomicCAS(&ctl->err, ERR_NONE, ERR_NONPHYSICAL);
-    else rate = cell_rate(P, Wn);
-  }
+  if (i < P.nx && j < P.ny) rate = update2d_cell(P, ctl, sv, sv.odd ? s1 : s0, sv.odd ? o0 : o1, FX, WX, FY, WY, WC, i, j);
   block_max_rate(rate, &ctl->rate_next, red);
 }
 
@@ -425,8 +100,10 @@ Scratch2D carve_scratch2d(const Params& P, double* base) {
 }
 
 void init_kernels2d() {
-  cudaFuncSetAttribute(xface2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
-  cudaFuncSetAttribute(yface2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
+  cudaFuncSetAttribute(xface2d_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
+  cudaFuncSetAttribute(yface2d_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
+  cudaFuncSetAttribute(xface2d_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
+  cudaFuncSetAttribute(yface2d_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
 }
 
 void launch_step2d(const Params& P, Ctl* ctl, const double* s0, const double* s1, double* o0,
@@ -437,10 +114,16 @@ void launch_step2d(const Params& P, Ctl* ctl, const double* s0, const double* s1
   coef2d_kernel<<<cg, cb, 0, st>>>(P, ctl, s0, s1, flag, S.ycoef, S.xcoef);
   if (ev) cudaEventRecord(ev[1], st);
   dim3 xg((P.nx + 1 + SEG - 1) / SEG, P.ny + 1, 4);
-  xface2d_kernel<<<xg, SEG, kFaceSmem, st>>>(P, ctl, S.ycoef, flag, S.FX, S.WX, S.WC);
+  if (P.flag_mode == FLAG_ALL_NONLINEAR)
+    xface2d_kernel<false><<<xg, SEG, kFaceSmem, st>>>(P, ctl, S.ycoef, flag, S.FX, S.WX, S.WC);
+  else
+    xface2d_kernel<true><<<xg, SEG, kFaceSmem, st>>>(P, ctl, S.ycoef, flag, S.FX, S.WX, S.WC);
   if (ev) cudaEventRecord(ev[2], st);
   dim3 yg((P.ny + 1 + SEG - 1) / SEG, P.nx, 3);
-  yface2d_kernel<<<yg, SEG, kFaceSmem, st>>>(P, ctl, S.xcoef, flag, S.FY, S.WY);
+  if (P.flag_mode == FLAG_ALL_NONLINEAR)
+    yface2d_kernel<false><<<yg, SEG, kFaceSmem, st>>>(P, ctl, S.xcoef, flag, S.FY, S.WY);
+  else
+    yface2d_kernel<true><<<yg, SEG, kFaceSmem, st>>>(P, ctl, S.xcoef, flag, S.FY, S.WY);
   if (ev) cudaEventRecord(ev[3], st);
   dim3 ug((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
   update2d_kernel<<<ug, cb, 0, st>>>(P, ctl, s0, s1, o0, o1, S.FX, S.WX, S.FY, S.WY, S.WC);

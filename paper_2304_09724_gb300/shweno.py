@@ -47,7 +47,9 @@ EXPORTS = ["shweno_create", "shweno_set_state", "shweno_get_state", "shweno_step
            "shweno_kernel_name", "shweno_cfl_dt", "shweno_get_time", "shweno_set_flags",
            "shweno_destroy", "shweno_last_error", "shweno_set_allocator", "shweno_step1d_noalloc",
            "shweno_flag_features", "shweno_weight_deviation", "shweno_mlp_forward", "shweno_mlp_grad",
-           "shweno_mlp_adam", "shweno_set_flag_net", "shweno_get_flags"]
+           "shweno_mlp_adam", "shweno_set_flag_net", "shweno_get_flags", "shweno_batch_create",
+           "shweno_batch_run", "shweno_batch_autotune", "shweno_batch_set", "shweno_batch_destroy",
+           "shweno_batch_last_error"]
 FLAG_FEATURES, FLAG_PARAMS = 22, 1825
 NOALLOC_MAX_NX = 65536
 
@@ -93,10 +95,18 @@ def lib():
                                   ctypes.c_float, ctypes.c_float, vp]
     L.shweno_set_flag_net.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int]
     L.shweno_get_flags.argtypes = [vp, vp, ctypes.c_int]
+    L.shweno_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
+    L.shweno_batch_run.argtypes = [vp, dp, ctypes.c_double, ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]
+    L.shweno_batch_autotune.argtypes = [vp, dp, ctypes.c_double, ctypes.c_int64, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int)]
+    L.shweno_batch_set.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64]
+    L.shweno_batch_destroy.argtypes = [vp]
+    L.shweno_batch_last_error.argtypes = [vp]
+    L.shweno_batch_last_error.restype = ctypes.c_char_p
     L.shweno_last_error.argtypes = [vp]
     L.shweno_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("shweno_last_error", "shweno_kernel_name"):
+        if name not in ("shweno_last_error", "shweno_kernel_name", "shweno_batch_last_error"):
             getattr(L, name).restype = st
     _lib = L
     return L
@@ -242,6 +252,53 @@ def shweno_destroy(h):
 
 def shweno_last_error(h=None):
     return lib().shweno_last_error(h).decode()
+
+
+class Batch:
+    """Many handles advanced by one persistent launch (shweno_batch_*)."""
+
+    def __init__(self, solvers, stream=0):
+        self.solvers = list(solvers)  # keeps the handles alive
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s.h.value for s in self.solvers])
+        b = ctypes.c_void_p()
+        st = lib().shweno_batch_create(arr, len(self.solvers), stream or None, ctypes.byref(b))
+        if st != OK:
+            raise ShwenoError(st, "shweno_batch_create failed")
+        self.b = b
+
+    def _err(self, st):
+        if st != OK:
+            raise ShwenoError(st, lib().shweno_batch_last_error(self.b).decode())
+
+    def run(self, t_final, cfl, max_steps=0, check=True):
+        n = len(self.solvers)
+        tf = (ctypes.c_double * n)(*([t_final] * n if np.isscalar(t_final) else list(t_final)))
+        per = (ctypes.c_int * n)()
+        st = lib().shweno_batch_run(self.b, tf, cfl, max_steps, per)
+        if check:
+            self._err(st)
+        return st, list(per)
+
+    def autotune(self, t_final, cfl, trial_steps=3):
+        n = len(self.solvers)
+        tf = (ctypes.c_double * n)(*([t_final] * n if np.isscalar(t_final) else list(t_final)))
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._err(lib().shweno_batch_autotune(self.b, tf, cfl, trial_steps, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def set(self, tile1d=0, ctas_per_sm=0, spin_limit=0):
+        self._err(lib().shweno_batch_set(self.b, tile1d, ctas_per_sm, spin_limit))
+
+    def close(self):
+        if self.b:
+            lib().shweno_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # --------------------------------------------------------------------------- convenience

@@ -1,0 +1,147 @@
+"""Batched persistent launch: many uneven problems in one persistent kernel give what each handle
+gives on its own (same status, same step count, states equal to round-off: the same device
+functions are inlined into two different kernels, whose FMA contraction may differ by an ulp),
+1D, 2D, mixed and with the learned flag; the autotuner leaves the states untouched; a
+device-side wait that runs out is reported as TIMEOUT and leaves every handle usable."""
+import numpy as np
+import pytest
+
+from paper_2304_09724_gb300 import shweno as S
+from paper_2304_09724_gb300 import workloads as WL
+from tests import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+def solo(wl, T, flag_net=None, max_steps=0):
+    """(state, (t, steps), status) of the handle run on its own."""
+    s = U.solver_of(wl, flag_mode=2 if flag_net else 0)
+    s.set_state(wl.state)
+    if flag_net:
+        S.shweno_set_flag_net(s.h, *flag_net)
+    status = S.OK
+    try:
+        if max_steps:
+            S.shweno_advance(s.h, max_steps, wl.cfl)
+            S.shweno_sync(s.h)
+        else:
+            s.run(T, wl.cfl)
+    except S.ShwenoError as e:
+        status = e.status
+    out = s.get_state(), s.time(), status
+    s.close()
+    return out
+
+
+def batch_of(wls, T, flag_net=None, max_steps=0, tile1d=0):
+    sols = []
+    for wl in wls:
+        s = U.solver_of(wl, flag_mode=2 if flag_net and wl.dim == 2 else 0)
+        s.set_state(wl.state)
+        if flag_net and wl.dim == 2:
+            S.shweno_set_flag_net(s.h, *flag_net)
+        sols.append(s)
+    b = S.Batch(sols)
+    if tile1d:
+        b.set(tile1d=tile1d)
+    st, per = b.run([T] * len(wls) if np.isscalar(T) else T, wls[0].cfl, max_steps=max_steps)
+    outs = [(s.get_state(), s.time()) for s in sols]
+    b.close()
+    for s in sols:
+        s.close()
+    return outs, per
+
+
+def same(a, b, wl, status=None):
+    """a: (state, (t, steps)) from the batch; b: solo (state, (t, steps), status)."""
+    if status is not None:
+        assert status == b[2]
+    assert a[1][1] == b[1][1]
+    assert a[1][0] == pytest.approx(b[1][0], rel=1e-12, abs=1e-300)
+    U.check(a[0], b[0], U.fields(wl), shocked=True, what=wl.name, wl=wl)
+
+
+@pytest.mark.parametrize("tile1d", [128, 512])
+def test_batch_1d_ragged_equals_solo(tile1d):
+    wls = [WL.random_riemann1d(s, nx=n) for s, n in zip(range(6), (40, 129, 300, 513, 77, 1000))]
+    outs, per = batch_of(wls, 0.03, tile1d=tile1d)
+    for wl, o, st in zip(wls, outs, per):
+        same(o, solo(wl, 0.03), wl, st)
+
+
+def test_batch_2d_and_mixed_equals_solo():
+    wls = [WL.riemann2d(n, WL.random_quadrants(s)) for s, n in zip((10, 11, 12), (24, 40, 70))]
+    wls.append(WL.vortex(32))
+    wls.append(WL.random_riemann1d(3, nx=200))
+    T = [0.02, 0.02, 0.02, 0.3, 0.02]
+    outs, per = batch_of(wls, T)
+    for wl, t, o, st in zip(wls, T, outs, per):
+        same(o, solo(wl, t), wl, st)
+
+
+def test_batch_learned_flag_equals_solo():
+    import torch
+
+    from paper_2304_09724_gb300 import flagnet as F
+
+    params, thr = F.load()
+    net = (torch.from_numpy(params).cuda(), thr)
+    wls = [WL.riemann2d(n, WL.random_quadrants(s)) for s, n in zip((20, 21), (48, 36))]
+    outs, per = batch_of(wls, 0.02, flag_net=net)
+    for wl, o, st in zip(wls, outs, per):
+        same(o, solo(wl, 0.02, flag_net=net), wl, st)
+
+
+def test_batch_max_steps_and_nonphysical_problem_stops_alone():
+    good = WL.random_riemann1d(4, nx=120)
+    bad = WL.random_riemann1d(5, nx=64)
+    bad.state["W"][2, 10] = -1.0  # negative energy: non-physical from the start
+    outs, per = batch_of([good, bad], 0.05, max_steps=7)
+    assert per[0] == S.OK and per[1] == S.E_NONPHYSICAL
+    assert outs[0][1][1] == 7
+    same(outs[0], solo(good, 0.05, max_steps=7), good, per[0])
+    assert outs[1][1] == (0.0, 0)
+
+
+def test_autotune_keeps_states():
+    wls = [WL.random_riemann1d(s, nx=n) for s, n in zip(range(30, 34), (100, 300, 700, 1500))]
+    sols = []
+    for wl in wls:
+        s = U.solver_of(wl)
+        s.set_state(wl.state)
+        sols.append(s)
+    b = S.Batch(sols)
+    tile, occ = b.autotune(0.05, wls[0].cfl, trial_steps=3)
+    assert tile in (128, 256, 512, 1024) and occ in (1, 2)
+    for wl, s in zip(wls, sols):
+        g = s.get_state()
+        assert np.array_equal(g["W"], wl.state["W"]) and s.time() == (0.0, 0)
+    st, per = b.run(0.02, wls[0].cfl)
+    for wl, s, pst in zip(wls, sols, per):
+        same((s.get_state(), s.time()), solo(wl, 0.02), wl, pst)
+    b.close()
+    for s in sols:
+        s.close()
+
+
+def test_wait_that_runs_out_reports_timeout_and_handles_stay_usable():
+    wls = [WL.random_riemann1d(s, nx=300) for s in range(40, 44)]
+    sols = []
+    for wl in wls:
+        s = U.solver_of(wl)
+        s.set_state(wl.state)
+        sols.append(s)
+    b = S.Batch(sols)
+    b.set(spin_limit=1)  # every CTA that finds the queue empty gives up at once
+    st, per = b.run(0.05, wls[0].cfl, check=False)
+    assert st == S.E_TIMEOUT
+    b.close()
+    # the committed state of every handle is consistent: continuing alone reaches the same result
+    for wl, s in zip(wls, sols):
+        try:
+            s.run(0.05, wl.cfl)
+            status = S.OK
+        except S.ShwenoError as e:
+            status = e.status
+        same((s.get_state(), s.time()), solo(wl, 0.05), wl, status)
+        s.close()
