@@ -103,6 +103,24 @@ def dist_init():
     return world, rank, local
 
 
+def reduce_max(x, world, device="cuda"):
+    """Maximum of x over the ranks (identity for one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, cells, steps, seconds):
+    """Whole-job cell-updates/s: every rank advanced `cells` cells `steps` times; the job took the
+    slowest rank's time."""
+    return world * cells * steps / seconds
+
+
 def oracle_sample(wl, window, steps):
     """Times the oracle (single-threaded C++) on a window x window block of the mesh, `steps`
     times; returns (cell-updates/s, seconds)."""
@@ -195,6 +213,108 @@ def learned_vs_plain(S, torch, WL, steps, warmup, vortex_wl):
     return out
 
 
+def bench_batched(args):
+    """Opt-in suite (--suite batched): the two batched workloads.
+    1D: 512 seeded Riemann problems (rho ~ U[0.1,2], u ~ U[-1,1], p ~ U[0.1,10], jump at 1/2,
+        outflow, N ~ U{400..16384}) in one persistent launch with autotuned tiles, `steps` steps
+        per problem, against advancing the handles one after another.
+    2D: 64 seeded four-quadrant problems (sides 512..2048), `steps` steps per problem, plain and
+        learned flag in one persistent launch each, against the plain per-instance solver."""
+    import numpy as np
+    import torch
+
+    from paper_2304_09724_gb300 import flagnet as F
+    from paper_2304_09724_gb300 import shweno as S
+    from paper_2304_09724_gb300 import workloads as WL
+
+    torch.cuda.set_device(0)
+    out = {"suite": "batched", "steps_per_problem": args.steps, "dtype": "f64", "data": "synthetic"}
+
+    def make(wls, learned=False, net=None):
+        sols = []
+        for wl in wls:
+            s = S.Solver(wl.dim, wl.eq, wl.nx, wl.ny, wl.domain, wl.bc, inflow=wl.inflow,
+                         flag_mode=2 if learned else 0)
+            s.set_state(wl.state)
+            if learned:
+                S.shweno_set_flag_net(s.h, torch.from_numpy(net[0]).cuda(), net[1])
+            sols.append(s)
+        torch.cuda.synchronize()
+        return sols
+
+    def updates(sols, before):
+        return sum(s.nx * s.ny * (s.time()[1] - b) for s, b in zip(sols, before))
+
+    def timed_batch(sols, T, tune):
+        b = S.Batch(sols)
+        tuned = b.autotune(T, CFL, trial_steps=2) if tune else None
+        before = [s.time()[1] for s in sols]
+        t0 = time.perf_counter()
+        st, per = b.run(T, CFL, max_steps=args.steps, check=False)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        n = updates(sols, before)
+        b.close()
+        return n / el, el, tuned, per
+
+    def timed_solo(sols):
+        before = [s.time()[1] for s in sols]
+        t0 = time.perf_counter()
+        for s in sols:
+            S.shweno_advance(s.h, args.steps, CFL)
+        for s in sols:
+            try:
+                S.shweno_sync(s.h)
+            except S.ShwenoError:
+                pass
+        el = time.perf_counter() - t0
+        return updates(sols, before) / el, el
+
+    # ---- 1D
+    wls = [WL.random_riemann1d(s) for s in range(512)]
+    sols = make(wls)
+    rate_b, el_b, tuned, per = timed_batch(sols, 0.15, True)
+    for s in sols:
+        s.close()
+    sols = make(wls)
+    rate_s, el_s = timed_solo(sols)
+    for s in sols:
+        s.close()
+    out["batched_1d_riemann_512"] = {
+        "cells": int(sum(w.nx for w in wls)), "batch_cell_updates_per_s": rate_b, "batch_s": el_b,
+        "per_instance_cell_updates_per_s": rate_s, "per_instance_s": el_s, "speedup": rate_b / rate_s,
+        "autotuned": {"tile1d": tuned[0], "ctas_per_sm": tuned[1]},
+        "nonphysical_problems": int(sum(1 for x in per if x == S.E_NONPHYSICAL))}
+    del wls
+    # ---- 2D
+    net = F.load()
+    wls = [WL.random_riemann2d(s) for s in range(args.c5_problems)]
+    res = {"problems": len(wls), "cells": int(sum(w.nx * w.ny for w in wls))}
+    for mode in ("plain", "learned"):
+        sols = make(wls, learned=(mode == "learned"), net=net)
+        r, el, _, per = timed_batch(sols, 0.25, False)
+        res[f"batch_{mode}_cell_updates_per_s"] = r
+        res[f"batch_{mode}_s"] = el
+        res[f"nonphysical_problems_{mode}"] = int(sum(1 for x in per if x == S.E_NONPHYSICAL))
+        if mode == "learned":
+            fr = []
+            for s in sols:
+                fl = np.empty((s.ny, s.nx), dtype=np.uint8)
+                S.shweno_get_flags(s.h, fl)
+                fr.append(fl.mean())
+            res["learned_flagged_fraction"] = float(np.mean(fr))
+        for s in sols:
+            s.close()
+    sols = make(wls)
+    r, el = timed_solo(sols)
+    for s in sols:
+        s.close()
+    res["per_instance_plain_cell_updates_per_s"] = r
+    res["per_instance_plain_s"] = el
+    out["batched_2d_quadrants"] = res
+    print(json.dumps(out), flush=True)
+
+
 def bench_gpu(args):
     import numpy as np
     import torch
@@ -235,18 +355,12 @@ def bench_gpu(args):
         S.shweno_sync(sol.h)
         torch.cuda.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1)
+    ms = reduce_max(e0.elapsed_time(e1), world)
     kernel_ms, timed_steps = S.shweno_get_timing(sol.h)
     S.shweno_set_timing(sol.h, False)
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     clocks = clk.summary()
     sec = ms / 1000.0
-    value = world * cells * args.steps / sec
+    value = job_value(world, cells, args.steps, sec)
 
     # end to end through the C ABI with host buffers: per step, copy the state in from pinned
     # host memory, take one CFL step, copy the state out
@@ -260,13 +374,7 @@ def bench_gpu(args):
         S.shweno_set_state(sol.h, host_in["W"], host_in["V"], host_in["Y"], host_in["Z"], 0.0)
         S.shweno_advance(sol.h, 1, CFL)
         S.shweno_get_state(sol.h, host_out["W"], host_out["V"], host_out["Y"], host_out["Z"])
-    e2e_sec = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([e2e_sec], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_sec = float(t.item())
+    e2e_sec = reduce_max(time.perf_counter() - t0, world)
     state_bytes = sum(v.numel() * 8 for v in host_in.values())
     assert np.isfinite(host_out["W"].numpy()).all()
     sol.close()
@@ -301,7 +409,7 @@ def bench_gpu(args):
         "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": pk.get("hbm_gbs", 6750.0),
                 "frac": hbm_gbs / pk.get("hbm_gbs", 6750.0), "bytes_per_cell_update": BYTES_PER_CELL_UPDATE},
         "clocks": clocks,
-        "e2e": {"value": world * cells * e2e_steps / e2e_sec, "unit": "cell-updates/s",
+        "e2e": {"value": job_value(world, cells, e2e_steps, e2e_sec), "unit": "cell-updates/s",
                 "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
         "gpu_launches": 3 + 6 * args.steps,
     }
@@ -325,9 +433,13 @@ def main():
     ap.add_argument("--ref-window", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--suite", default="main", choices=["main", "batched"])
+    ap.add_argument("--c5-problems", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
+    elif args.suite == "batched":
+        bench_batched(args)
     else:
         bench_gpu(args)
 
