@@ -123,6 +123,44 @@ def burgers_sine(nx, t_final=0.5 / math.pi, cfl=0.6):
                     exact=exact)
 
 
+def burgers2d_sine(n, t_final=0.25 / math.pi, cfl=0.6):
+    """u_t + (u^2/2)_x + (u^2/2)_y = 0 on (0,2)^2, u0 = 0.5 + sin(pi (x + y)), periodic: the 2D
+    scalar law of Section 3 with the data of Example 5.1 laid along the diagonal.  The solution
+    is u = u0(x + y - 2 u t) (smooth until t = 1/(2 pi)); T defaults to half of that."""
+    f = lambda x, y: (0.5 + np.sin(np.pi * (x + y)))[None]
+    W, V, Y, Z = project_2d(f, 0.0, 2.0, 0.0, 2.0, n, n)
+
+    def exact(t, nq=6):
+        def u_at(x, y):
+            s = x + y
+            u = 0.5 + np.sin(np.pi * s)
+            for _ in range(100):
+                g = u - 0.5 - np.sin(np.pi * (s - 2.0 * u * t))
+                dg = 1.0 + 2.0 * np.pi * t * np.cos(np.pi * (s - 2.0 * u * t))
+                du = g / dg
+                u = u - du
+                if np.max(np.abs(du)) < 1e-15:
+                    break
+            return u[None]
+        return project_2d(u_at, 0.0, 2.0, 0.0, 2.0, n, n, nq)[0]
+
+    return Workload("burgers2d_sine", 2, BURGERS, n, n, (0.0, 2.0, 0.0, 2.0), (PERIODIC,) * 4,
+                    t_final, cfl, {"W": W, "V": V, "Y": Y, "Z": Z}, exact=exact)
+
+
+def burgers2d_riemann(n, values=(-1.0, -0.2, 0.5, 0.8), t_final=0.5, cfl=0.6):
+    """Four-quadrant Riemann problem of 2D Burgers on (0,1)^2, split at (1/2, 1/2), outflow
+    sides; values for the quadrants NE, NW, SW, SE (shocks, rarefactions and a sonic point)."""
+    if n % 2:
+        raise ValueError("n must be even: the split lines are then cell edges")
+    W = np.empty((1, n, n))
+    h = n // 2
+    W[0, h:, h:], W[0, h:, :h], W[0, :h, :h], W[0, :h, h:] = values
+    Z0 = np.zeros_like(W)
+    return Workload("burgers2d_riemann", 2, BURGERS, n, n, (0.0, 1.0, 0.0, 1.0), (OUTFLOW,) * 4,
+                    t_final, cfl, {"W": W, "V": Z0, "Y": Z0.copy(), "Z": Z0.copy()}, shocked=True)
+
+
 # --------------------------------------------------------------------------- Example 5.2
 def euler1d_sine(nx, t_final=10.0, cfl=0.6):
     """rho = 1 + 0.2 sin(pi x), u = p = 1 on (0,2), periodic (Example 5.2); exact: translation."""
@@ -355,7 +393,8 @@ def random_smooth_1d(seed, nx, eq=EULER, amp=0.1):
     return project_1d(f, 0.0, 1.0, nx)
 
 
-def random_smooth_2d(seed, nx, ny, amp=0.1):
+def random_smooth_2d(seed, nx, ny, amp=0.1, eq=EULER):
+    """Seeded smooth periodic data on (0,1)^2 (Burgers: a field that changes sign)."""
     rng = np.random.default_rng(50_000 + seed)
     kx = rng.integers(1, 3, size=4)
     ky = rng.integers(0, 3, size=4)
@@ -364,5 +403,7 @@ def random_smooth_2d(seed, nx, ny, amp=0.1):
 
     def f(x, y):
         m = [a[c] * np.sin(2 * math.pi * (kx[c] * x + ky[c] * y) + ph[c]) for c in range(4)]
+        if eq == BURGERS:
+            return (0.1 + 5 * m[0] + 3 * m[1] + 0 * y)[None]
         return euler_conserved(1.0 + m[0], 0.4 + m[1], 1.0 + m[2], -0.3 + m[3])
     return project_2d(f, 0.0, 1.0, 0.0, 1.0, nx, ny)
