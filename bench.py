@@ -31,12 +31,14 @@ sys.path.insert(0, ROOT)
 CFL = 0.6
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP64_SLOTS_PER_S = 152 * 2 * 2.070e9  # FP64 thread instructions per second (DFMA, DMUL, DADD alike)
 FP64_MEASURED_TFLOPS = 1.1935  # DFMA microbenchmark on this machine's GB300 (all SMs busy)
 # FP64 operations (DFMA counted as 2) per x-face point of xface2d, from the ncu instruction
 # counters of the committed kernel (profiles/xface2d_vortex512.md), and its DRAM bytes per point
 # from the same capture (512^2; traffic grows in proportion to the points).
-FLOPS_PER_XFACE_POINT = 6134
-DRAM_BYTES_PER_XFACE_POINT = 346.1
+FLOPS_PER_XFACE_POINT = 5887
+FP64_INST_PER_XFACE_POINT = 3470  # DFMA + DMUL + DADD thread instructions (each one pipe slot)
+DRAM_BYTES_PER_XFACE_POINT = 346.6
 BYTES_PER_CELL_UPDATE = 256  # 16 doubles read + 16 written per cell (ideal reuse)
 
 
@@ -394,6 +396,7 @@ def bench_gpu(args):
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": DRAM_BYTES_PER_XFACE_POINT * xpoints,
                 "flops_per_launch": flops, "launch_ms": dom_ms,
+                "fp64_pipe_slot_frac": FP64_INST_PER_XFACE_POINT * xpoints / (dom_ms / 1000.0) / FP64_SLOTS_PER_S,
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe)"}
     hbm_gbs = cells * BYTES_PER_CELL_UPDATE / (sec / (world * args.steps)) / 1e9 / world
     line = {

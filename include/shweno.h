@@ -62,8 +62,8 @@ typedef enum {
   SHWENO_BC_OUTFLOW = 1,
   SHWENO_BC_REFLECTIVE = 2,
   SHWENO_BC_INFLOW = 3,
-  SHWENO_BC_DMR_BOTTOM = 4,
-  SHWENO_BC_DMR_TOP = 5
+  SHWENO_BC_DMR_BOTTOM = 4,  /* Euler only, y-low side */
+  SHWENO_BC_DMR_TOP = 5      /* Euler only, y-high side */
 } shweno_bc_kind;
 
 typedef struct {

@@ -281,10 +281,11 @@ shweno_status shweno_create(const shweno_grid* grid, double gamma, const shweno_
   if (!(grid->x1 > grid->x0) || (dim == 2 && !(grid->y1 > grid->y0)))
     return fail(nullptr, SHWENO_E_INVALID, "empty domain");
   if (grid->eq == SHWENO_EULER && !(gamma > 1.0)) return fail(nullptr, SHWENO_E_INVALID, "gamma must be > 1");
-  if (dim == 2 && grid->eq == SHWENO_BURGERS)
-    return fail(nullptr, SHWENO_E_INVALID, "2D Burgers is not provided by this library");
-  for (int s = 0; s < (dim == 2 ? 4 : 2); ++s)
+  for (int s = 0; s < (dim == 2 ? 4 : 2); ++s) {
     if (!valid_bc(bc->kind[s], dim, s)) return fail(nullptr, SHWENO_E_INVALID, "invalid boundary condition");
+    if (grid->eq == SHWENO_BURGERS && (bc->kind[s] == SHWENO_BC_DMR_BOTTOM || bc->kind[s] == SHWENO_BC_DMR_TOP))
+      return fail(nullptr, SHWENO_E_INVALID, "the double Mach reflection boundaries carry Euler states");
+  }
   for (int a = 0; a < dim; ++a)
     if ((bc->kind[2 * a] == SHWENO_BC_PERIODIC) != (bc->kind[2 * a + 1] == SHWENO_BC_PERIODIC))
       return fail(nullptr, SHWENO_E_INVALID, "periodic boundaries must be paired");

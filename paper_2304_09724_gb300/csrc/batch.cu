@@ -160,9 +160,13 @@ __device__ void do_item(const BatchProblem& B, int kind, long long idx, unsigned
     }
     case PH_COEF: {
       const int bxi = (int)(idx % B.ncx), byi = (int)(idx / B.ncx);
-      coef2d_item<TYB>(P, sv, B.s0, B.s1, B.flag, B.S.ycoef, B.S.xcoef, bxi * TX - 2, byi * TYB - 2,
-                       reinterpret_cast<double(*)[TYB + 2][TX + 2]>(smem), threadIdx.x % TX,
-                       threadIdx.x / TX);
+      auto tile = reinterpret_cast<double(*)[TYB + 2][TX + 2]>(smem);
+      if (P.ncomp == 1)
+        coef2d_item<1, TYB>(P, sv, B.s0, B.s1, B.flag, B.S.ycoef, B.S.xcoef, bxi * TX - 2, byi * TYB - 2,
+                            tile, threadIdx.x % TX, threadIdx.x / TX);
+      else
+        coef2d_item<4, TYB>(P, sv, B.s0, B.s1, B.flag, B.S.ycoef, B.S.xcoef, bxi * TX - 2, byi * TYB - 2,
+                            tile, threadIdx.x % TX, threadIdx.x / TX);
       break;
     }
     case PH_FACE: {
@@ -171,14 +175,26 @@ __device__ void do_item(const BatchProblem& B, int kind, long long idx, unsigned
         const int seg = (int)(idx % B.nsegx), r = (int)(idx / B.nsegx);
         const int slice = r < 3 * P.ny ? r / P.ny : 3;
         const int row = r < 3 * P.ny ? r % P.ny : r - 3 * P.ny;
-        if (flags) xface_item<true>(P, sv, B.S.ycoef, B.flag, B.S.FX, B.S.WX, B.S.WC, seg * SEG, row, slice, smem);
-        else xface_item<false>(P, sv, B.S.ycoef, B.flag, B.S.FX, B.S.WX, B.S.WC, seg * SEG, row, slice, smem);
+        const int f0 = seg * SEG;
+        if (P.ncomp == 1) {
+          if (flags) xface_item<1, true>(P, sv, B.S.ycoef, B.flag, B.S.FX, B.S.WX, B.S.WC, f0, row, slice, smem);
+          else xface_item<1, false>(P, sv, B.S.ycoef, B.flag, B.S.FX, B.S.WX, B.S.WC, f0, row, slice, smem);
+        } else {
+          if (flags) xface_item<4, true>(P, sv, B.S.ycoef, B.flag, B.S.FX, B.S.WX, B.S.WC, f0, row, slice, smem);
+          else xface_item<4, false>(P, sv, B.S.ycoef, B.flag, B.S.FX, B.S.WX, B.S.WC, f0, row, slice, smem);
+        }
       } else {
         const long long k = idx - B.nxitems;
         const int seg = (int)(k % B.nsegy), r = (int)(k / B.nsegy);
         const int slice = r / P.nx, col = r % P.nx;
-        if (flags) yface_item<true>(P, sv, B.S.xcoef, B.flag, B.S.FY, B.S.WY, seg * SEG, col, slice, smem);
-        else yface_item<false>(P, sv, B.S.xcoef, B.flag, B.S.FY, B.S.WY, seg * SEG, col, slice, smem);
+        const int f0 = seg * SEG;
+        if (P.ncomp == 1) {
+          if (flags) yface_item<1, true>(P, sv, B.S.xcoef, B.flag, B.S.FY, B.S.WY, f0, col, slice, smem);
+          else yface_item<1, false>(P, sv, B.S.xcoef, B.flag, B.S.FY, B.S.WY, f0, col, slice, smem);
+        } else {
+          if (flags) yface_item<4, true>(P, sv, B.S.xcoef, B.flag, B.S.FY, B.S.WY, f0, col, slice, smem);
+          else yface_item<4, false>(P, sv, B.S.xcoef, B.flag, B.S.FY, B.S.WY, f0, col, slice, smem);
+        }
       }
       break;
     }
@@ -186,9 +202,13 @@ __device__ void do_item(const BatchProblem& B, int kind, long long idx, unsigned
       const int seg = (int)(idx % B.nsegu), j = (int)(idx / B.nsegu);
       const int i = seg * BT + threadIdx.x;
       double rate = 0.0;
-      if (i < P.nx)
-        rate = update2d_cell(P, ctl, sv, sv.odd ? B.s1 : B.s0, sv.odd ? B.s0 : B.s1, B.S.FX, B.S.WX, B.S.FY,
-                             B.S.WY, B.S.WC, i, j);
+      if (i < P.nx) {
+        const double* st = sv.odd ? B.s1 : B.s0;
+        double* out = sv.odd ? B.s0 : B.s1;
+        rate = P.ncomp == 1
+                   ? update2d_cell<1>(P, ctl, sv, st, out, B.S.FX, B.S.WX, B.S.FY, B.S.WY, B.S.WC, i, j)
+                   : update2d_cell<4>(P, ctl, sv, st, out, B.S.FX, B.S.WX, B.S.FY, B.S.WY, B.S.WC, i, j);
+      }
       block_max_rate(rate, &ctl->rate_next, red);
       break;
     }

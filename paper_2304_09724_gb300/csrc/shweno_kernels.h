@@ -10,8 +10,8 @@ namespace shweno {
 
 // Scratch buffers of one 2D step (all device memory owned by the handle).
 struct Scratch2D {
-  double* ycoef;  // [2 sets][4 comps][5 coefs][ny+2][nx+4]
-  double* xcoef;  // [2 sets][4 comps][5 coefs][nx][ny+4]
+  double* ycoef;  // [2 sets][ncomp][5 coefs][ny+2][nx+4]
+  double* xcoef;  // [2 sets][ncomp][5 coefs][nx][ny+4]
   double* FX;     // [3 gauss][ncomp][ny][nx+1]  time-averaged x-flux per Gauss point
   double* WX;     // [3 gauss][ncomp][ny][nx+1]  state at t_{n+1} per Gauss point
   double* FY;     // [3 gauss][ncomp][ny+1][nx]

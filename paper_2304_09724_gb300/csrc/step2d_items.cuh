@@ -11,7 +11,7 @@ constexpr int SPAN = SEG + 3;  // first-pass evaluations a CTA needs
 constexpr int TX = 32;         // first-pass tile width
 
 // ------------------------------------------------------------------ one face point
-// Second pass across the face.  ev[set*4+q][k][col] holds the first-pass Taylor coefficients
+// Second pass across the face.  ev[set*NC+q][k][col] holds the first-pass Taylor coefficients
 // (order k along the face) of a row of stencil columns.  Each cell's weights come from its
 // order-0 data and serve every order (remark ending Section 2.1.2) and both of the cell's faces:
 // they are computed once per cell (cell_mixes) into shared memory.
@@ -25,17 +25,17 @@ constexpr size_t kFaceSmem = kEvBytes + sizeof(MixTable);
 
 // Weights of the cells in columns 1..SEG+1 (the cells whose faces the CTA owns).  nl(col)
 // returns whether the cell of column col uses the nonlinear weights.
-template <typename FlagOf>
+template <int NC, typename FlagOf>
 __device__ __forceinline__ void cell_mixes(const Params& P, const double (*ev)[5][SPAN],
                                            MixTable& mt, FlagOf nl) {
-  for (int it = threadIdx.x; it < 4 * (SEG + 1); it += SEG) {
+  for (int it = threadIdx.x; it < NC * (SEG + 1); it += SEG) {
     const int q = it / (SEG + 1), c = 1 + it % (SEG + 1);
     const int nonlinear = nl(c);
     if (q == 0) mt.lin[c] = !nonlinear;
     if (!nonlinear) continue;
     const double Wm = ev[q][0][c - 1], W0 = ev[q][0][c], Wp = ev[q][0][c + 1];
     double cf[5];
-    p1_coeffs(Wm, W0, Wp, ev[4 + q][0][c - 1], ev[4 + q][0][c + 1], cf);
+    p1_coeffs(Wm, W0, Wp, ev[NC + q][0][c - 1], ev[NC + q][0][c + 1], cf);
     const Mix m = shweno_mix(P, Wm, W0, Wp, cf, 1);
     mt.A[q][c] = m.A;
     mt.B[q][c] = m.B;
@@ -48,12 +48,12 @@ __device__ __forceinline__ void cell_mixes(const Params& P, const double (*ev)[5
 //   e[p] = A * END[p] . data + (small-stencil terms for p <= 1),
 // with END the constant rows of p1's Taylor coefficients at the end and data = (W-, W0, W+,
 // v-, v+) of order k.
-template <bool PLUS>
+template <int NC, bool PLUS>
 __device__ __forceinline__ void side_out(const double (*ev)[5][SPAN], int c0, int q, int k, double A,
                                          double B, double C, bool lin, double e[5]) {
   using namespace shweno_tables;
-  const double d[5] = {ev[q][k][c0], ev[q][k][c0 + 1], ev[q][k][c0 + 2], ev[4 + q][k][c0],
-                       ev[4 + q][k][c0 + 2]};
+  const double d[5] = {ev[q][k][c0], ev[q][k][c0 + 1], ev[q][k][c0 + 2], ev[NC + q][k][c0],
+                       ev[NC + q][k][c0 + 2]};
   if (lin) {  // linear weights: p = p1
 #pragma unroll
     for (int p = 0; p + k <= 4; ++p) e[p] = end_dot<PLUS>(p, d);
@@ -67,63 +67,66 @@ __device__ __forceinline__ void side_out(const double (*ev)[5][SPAN], int c0, in
   if (k <= 3) e[1] += (B - C) * d[1] - B * d[0] + C * d[2];
 }
 
-// Face point: both sides' second pass, HLLC, upwinding, CK; returns the time-Taylor
-// coefficients tc[q][0..4].  Left cell in column c0 + 1, right cell in c0 + 2.  dir = 0: x-face
-// (first pass along y), 1: y-face.
-template <bool FLAGS>
+// Face point: both sides' second pass, leading term (Burgers: exact Godunov state; Euler:
+// HLLC), upwinding, CK; returns the time-Taylor coefficients tc[q][0..4].  Left cell in column
+// c0 + 1, right cell in c0 + 2.  dir = 0: x-face (first pass along y), 1: y-face.  NC = 1
+// (Burgers, F = G = u^2/2) or 4 (Euler).
+template <int NC, bool FLAGS>
 __device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5][SPAN],
-                                           const MixTable& mt, int c0, int dir, double tc[4][5]) {
+                                           const MixTable& mt, int c0, int dir, double tc[NC][5]) {
   const double g = P.gamma;
-  double a[4][25];
-  double dl[4][5], dr[4][5];
-  double AL[4], BL[4], CL[4], AR[4], BR[4], CR[4];
+  double a[NC][25];
+  double dl[NC][5], dr[NC][5];
+  double AL[NC], BL[NC], CL[NC], AR[NC], BR[NC], CR[NC];
   // FLAGS = false: every cell uses the nonlinear weights (compile-time, no branch)
   const bool linL = FLAGS && mt.lin[c0 + 1], linR = FLAGS && mt.lin[c0 + 2];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < NC; ++q) {
     AL[q] = linL ? 1.0 : mt.A[q][c0 + 1]; BL[q] = linL ? 0.0 : mt.B[q][c0 + 1]; CL[q] = linL ? 0.0 : mt.C[q][c0 + 1];
     AR[q] = linR ? 1.0 : mt.A[q][c0 + 2]; BR[q] = linR ? 0.0 : mt.B[q][c0 + 2]; CR[q] = linR ? 0.0 : mt.C[q][c0 + 2];
   }
   // tangential order 0 first: it carries the leading-term data
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    side_out<true>(ev, c0, q, 0, AL[q], BL[q], CL[q], linL, dl[q]);
-    side_out<false>(ev, c0 + 1, q, 0, AR[q], BR[q], CR[q], linR, dr[q]);
+  for (int q = 0; q < NC; ++q) {
+    side_out<NC, true>(ev, c0, q, 0, AL[q], BL[q], CL[q], linL, dl[q]);
+    side_out<NC, false>(ev, c0 + 1, q, 0, AR[q], BR[q], CR[q], linR, dr[q]);
   }
-  double WL[4], WR[4], Ws[4];
+  double WL[NC], WR[NC], Ws[NC];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) { WL[q] = dl[q][0]; WR[q] = dr[q][0]; }
-  hllc_state<4>(WL, WR, g, dir, Ws);
-  Upwinder<4> U;
-  U.setup(Ws, g, dir);
+  for (int q = 0; q < NC; ++q) { WL[q] = dl[q][0]; WR[q] = dr[q][0]; }
+  if constexpr (NC == 1) Ws[0] = burgers_godunov(WL[0], WR[0]);  // the same flux u^2/2 along x and y
+  else hllc_state<NC>(WL, WR, g, dir, Ws);
+  Upwinder<NC> U;
+  U.setup(Ws, g, dir, NC == 1 ? fmax(fabs(WL[0]), fabs(WR[0])) : 0.0);
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     if (k > 0) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        side_out<true>(ev, c0, q, k, AL[q], BL[q], CL[q], linL, dl[q]);
-        side_out<false>(ev, c0 + 1, q, k, AR[q], BR[q], CR[q], linR, dr[q]);
+      for (int q = 0; q < NC; ++q) {
+        side_out<NC, true>(ev, c0, q, k, AL[q], BL[q], CL[q], linL, dl[q]);
+        side_out<NC, false>(ev, c0 + 1, q, k, AR[q], BR[q], CR[q], linR, dr[q]);
       }
     }
 #pragma unroll
     for (int p = 0; p + k <= 4; ++p) {
       if (p == 0 && k == 0) continue;
-      double x[4], y[4], o[4];
+      double x[NC], y[NC], o[NC];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) { x[q] = dl[q][p]; y[q] = dr[q][p]; }
+      for (int q = 0; q < NC; ++q) { x[q] = dl[q][p]; y[q] = dr[q][p]; }
       U.apply(x, y, o);
       // p is the order across the face, k the order along it
       const int idx = dir == 0 ? p * 5 + k : k * 5 + p;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) a[q][idx] = o[q];
+      for (int q = 0; q < NC; ++q) a[q][idx] = o[q];
     }
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) a[q][0] = Ws[q];
-  double t4[4][5];
-  ck_euler2d(a, t4, P.ckx, P.cky, g - 1.0);
+  for (int q = 0; q < NC; ++q) a[q][0] = Ws[q];
+  double t4[NC][5];
+  if constexpr (NC == 1) ck_burgers2d(a, t4, P.ckx, P.cky, g - 1.0);
+  else ck_euler2d(a, t4, P.ckx, P.cky, g - 1.0);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < NC; ++q) {
     tc[q][0] = Ws[q];
 #pragma unroll
     for (int k = 1; k < 5; ++k) tc[q][k] = t4[q][k];
@@ -131,26 +134,27 @@ __device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5
 }
 
 // Lobatto time average of the flux along dir and the state at tau = dt.
-__device__ __forceinline__ void lobatto(const double tc[4][5], double dt, double g, int dir,
-                                        double Fh[4], double We[4]) {
+template <int NC>
+__device__ __forceinline__ void lobatto(const double tc[NC][5], double dt, double g, int dir,
+                                        double Fh[NC], double We[NC]) {
   using namespace shweno_tables;
   const double taus[4] = {0.0, LOB_L1 * dt, LOB_L2 * dt, dt};
   const double wts[4] = {LOB_W0, LOB_W1, LOB_W1, LOB_W0};
 #pragma unroll
-  for (int q = 0; q < 4; ++q) Fh[q] = 0.0;
+  for (int q = 0; q < NC; ++q) Fh[q] = 0.0;
 #pragma unroll
   for (int al = 0; al < 4; ++al) {
-    double W[4], F[4];
+    double W[NC], F[NC];
     const double tau = taus[al];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < NC; ++q)
       W[q] = (((tc[q][4] * tau + tc[q][3]) * tau + tc[q][2]) * tau + tc[q][1]) * tau + tc[q][0];
-    phys_flux<4>(W, g, dir, F);
+    phys_flux<NC>(W, g, dir, F);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) Fh[q] += wts[al] * F[q];
+    for (int q = 0; q < NC; ++q) Fh[q] += wts[al] * F[q];
     if (al == 3) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) We[q] = W[q];
+      for (int q = 0; q < NC; ++q) We[q] = W[q];
     }
   }
 }
@@ -160,9 +164,9 @@ __device__ __forceinline__ double state_at(const double tc[5], double tau) {
 }
 
 // First-pass polynomials of the cells of one tile: thread (tx, ty) of a TX x TYB block owns the
-// extended cell (bx + tx, by + ty); the 16 fields of the tile plus a one-cell halo are staged in
-// shared memory `tile` by all nthreads threads first.
-template <int TYB>
+// extended cell (bx + tx, by + ty); the 4 * NC fields of the tile plus a one-cell halo are staged
+// in shared memory `tile` (room for 16) by all nthreads threads first.
+template <int NC, int TYB>
 __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv, const double* s0,
                                             const double* s1, const uint8_t* __restrict__ flag,
                                             double* __restrict__ ycoef, double* __restrict__ xcoef,
@@ -171,12 +175,12 @@ __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv,
   const double* st = sv.odd ? s1 : s0;
   const double t = sv.t;
   const int tid = ty * TX + tx;
-  for (int idx = tid; idx < 16 * (TYB + 2) * (TX + 2); idx += TX * TYB) {
+  for (int idx = tid; idx < 4 * NC * (TYB + 2) * (TX + 2); idx += TX * TYB) {
     const int xx = idx % (TX + 2), rest = idx / (TX + 2);
     const int yy = rest % (TYB + 2), fq = rest / (TYB + 2);
     const int i = bx - 1 + xx, j = by - 1 + yy;
     double v = 0.0;
-    if (i >= -3 && i <= P.nx + 2 && j >= -3 && j <= P.ny + 2) v = fetch(P, st, fq >> 2, fq & 3, i, j, t);
+    if (i >= -3 && i <= P.nx + 2 && j >= -3 && j <= P.ny + 2) v = fetch(P, st, fq / NC, fq % NC, i, j, t);
     tile[fq][yy][xx] = v;
   }
   __syncthreads();
@@ -188,8 +192,8 @@ __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv,
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int fa = (s == 0 ? 0 : 1) * 4 + q, fd = (s == 0 ? 2 : 3) * 4 + q;
+      for (int q = 0; q < NC; ++q) {
+        const int fa = (s == 0 ? 0 : 1) * NC + q, fd = (s == 0 ? 2 : 3) * NC + q;
         const double Wm = tile[fa][ly - 1][lx], W0 = tile[fa][ly][lx], Wp = tile[fa][ly + 1][lx];
         const double vm = P.dy * tile[fd][ly - 1][lx], vp = P.dy * tile[fd][ly + 1][lx];
         double c[5], C[5];
@@ -198,7 +202,7 @@ __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv,
         const double sc = s == 0 ? 1.0 : P.dx;  // x-pass derivative data: dx * avg(W_x)
 #pragma unroll
         for (int k = 0; k < 5; ++k)
-          ycoef[((size_t)((s * 4 + q) * 5 + k) * NY2 + (jr + 1)) * NX4 + (ic + 2)] = sc * C[k];
+          ycoef[((size_t)((s * NC + q) * 5 + k) * NY2 + (jr + 1)) * NX4 + (ic + 2)] = sc * C[k];
       }
   }
   if (ic >= 0 && ic < P.nx && jr <= P.ny + 1) {  // x-pass: {W,V} and {Y,Z} along a row
@@ -206,8 +210,8 @@ __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv,
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int fa = (s == 0 ? 0 : 2) * 4 + q, fd = (s == 0 ? 1 : 3) * 4 + q;
+      for (int q = 0; q < NC; ++q) {
+        const int fa = (s == 0 ? 0 : 2) * NC + q, fd = (s == 0 ? 1 : 3) * NC + q;
         const double Wm = tile[fa][ly][lx - 1], W0 = tile[fa][ly][lx], Wp = tile[fa][ly][lx + 1];
         const double vm = P.dx * tile[fd][ly][lx - 1], vp = P.dx * tile[fd][ly][lx + 1];
         double c[5], C[5];
@@ -216,14 +220,14 @@ __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv,
         const double sc = s == 0 ? 1.0 : P.dy;  // y-pass derivative data: dy * avg(W_y)
 #pragma unroll
         for (int k = 0; k < 5; ++k)
-          xcoef[((size_t)((s * 4 + q) * 5 + k) * P.nx + ic) * NY4 + (jr + 2)] = sc * C[k];
+          xcoef[((size_t)((s * NC + q) * 5 + k) * P.nx + ic) * NY4 + (jr + 2)] = sc * C[k];
       }
   }
 }
 
 // x-face Gauss points (slice 0..2, cell row `row`) or corner points (slice 3, corner row `row`
 // at y_{row-1/2}) of faces x_{f0-1/2} .. x_{f0+SEG-3/2}; SEG threads, smem_raw of kFaceSmem bytes.
-template <bool FLAGS>
+template <int NC, bool FLAGS>
 __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv,
                                            const double* __restrict__ ycoef,
                                            const uint8_t* __restrict__ flag, double* __restrict__ FX,
@@ -233,7 +237,7 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv,
   MixTable& mt = *reinterpret_cast<MixTable*>(smem_raw + kEvBytes);
   const int NX4 = P.nx + 4, NY2 = P.ny + 2;
   using namespace shweno_tables;
-  for (int it = threadIdx.x; it < 8 * SPAN; it += SEG) {
+  for (int it = threadIdx.x; it < 2 * NC * SPAN; it += SEG) {
     const int col = it % SPAN, rq = it / SPAN;
     const int tcol = f0 + col;
     double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -259,7 +263,7 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv,
   }
   __syncthreads();
   // cell column c holds cell i = f0 + c - 2; a corner row uses the rows below and above
-  cell_mixes(P, ev, mt, [&](int c) {
+  cell_mixes<NC>(P, ev, mt, [&](int c) {
     const int i = f0 + c - 2;
     return slice < 3 ? cell_flag(P, flag, i, row)
                      : (cell_flag(P, flag, i, row - 1) | cell_flag(P, flag, i, row));
@@ -267,26 +271,26 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv,
   __syncthreads();
   const int fi = f0 + threadIdx.x;  // face x_{fi-1/2}
   if (fi > P.nx) return;  // no barrier follows
-  double tc[4][5];
-  face_point<FLAGS>(P, ev, mt, threadIdx.x, 0, tc);
+  double tc[NC][5];
+  face_point<NC, FLAGS>(P, ev, mt, threadIdx.x, 0, tc);
   const double dt = sv.dt;
   if (slice < 3) {
-    double Fh[4], We[4];
-    lobatto(tc, dt, P.gamma, 0, Fh, We);
+    double Fh[NC], We[NC];
+    lobatto<NC>(tc, dt, P.gamma, 0, Fh, We);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const size_t o = ((size_t)(slice * 4 + q) * P.ny + row) * (P.nx + 1) + fi;
+    for (int q = 0; q < NC; ++q) {
+      const size_t o = ((size_t)(slice * NC + q) * P.ny + row) * (P.nx + 1) + fi;
       FX[o] = Fh[q];
       WX[o] = We[q];
     }
   } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) WC[((size_t)q * (P.ny + 1) + row) * (P.nx + 1) + fi] = state_at(tc[q], dt);
+    for (int q = 0; q < NC; ++q) WC[((size_t)q * (P.ny + 1) + row) * (P.nx + 1) + fi] = state_at(tc[q], dt);
   }
 }
 
 // y-face Gauss points (slice 0..2) of column `col`, faces y_{f0-1/2} .. y_{f0+SEG-3/2}.
-template <bool FLAGS>
+template <int NC, bool FLAGS>
 __device__ __forceinline__ void yface_item(const Params& P, const StepView& sv,
                                            const double* __restrict__ xcoef,
                                            const uint8_t* __restrict__ flag, double* __restrict__ FY,
@@ -296,7 +300,7 @@ __device__ __forceinline__ void yface_item(const Params& P, const StepView& sv,
   MixTable& mt = *reinterpret_cast<MixTable*>(smem_raw + kEvBytes);
   const int NY4 = P.ny + 4;
   using namespace shweno_tables;
-  for (int it = threadIdx.x; it < 8 * SPAN; it += SEG) {
+  for (int it = threadIdx.x; it < 2 * NC * SPAN; it += SEG) {
     const int r = it % SPAN, rq = it / SPAN;
     const int trow = f0 + r;
     double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -310,17 +314,17 @@ __device__ __forceinline__ void yface_item(const Params& P, const StepView& sv,
     for (int k = 0; k < 5; ++k) ev[rq][k][r] = e[k];
   }
   __syncthreads();
-  cell_mixes(P, ev, mt, [&](int c) { return cell_flag(P, flag, col, f0 + c - 2); });
+  cell_mixes<NC>(P, ev, mt, [&](int c) { return cell_flag(P, flag, col, f0 + c - 2); });
   __syncthreads();
   const int fj = f0 + threadIdx.x;  // face y_{fj-1/2}
   if (fj > P.ny) return;
-  double tc[4][5];
-  face_point<FLAGS>(P, ev, mt, threadIdx.x, 1, tc);
-  double Gh[4], We[4];
-  lobatto(tc, sv.dt, P.gamma, 1, Gh, We);
+  double tc[NC][5];
+  face_point<NC, FLAGS>(P, ev, mt, threadIdx.x, 1, tc);
+  double Gh[NC], We[NC];
+  lobatto<NC>(tc, sv.dt, P.gamma, 1, Gh, We);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const size_t o = ((size_t)(slice * 4 + q) * (P.ny + 1) + fj) * P.nx + col;
+  for (int q = 0; q < NC; ++q) {
+    const size_t o = ((size_t)(slice * NC + q) * (P.ny + 1) + fj) * P.nx + col;
     FY[o] = Gh[q];
     WY[o] = We[q];
   }
@@ -328,6 +332,7 @@ __device__ __forceinline__ void yface_item(const Params& P, const StepView& sv,
 
 // Update of cell (i, j) (Eq. 3.2, 3.10) into `out`; returns the cell's CFL rate (0 when the new
 // state is non-physical, which raises the control block's error word).
+template <int NC>
 __device__ __forceinline__ double update2d_cell(const Params& P, Ctl* __restrict__ ctl, const StepView& sv,
                                                 const double* st,
                                                 double* out, const double* __restrict__ FX,
@@ -339,15 +344,15 @@ __device__ __forceinline__ double update2d_cell(const Params& P, Ctl* __restrict
   const int nx = P.nx, ny = P.ny;
   using namespace shweno_tables;
   const double gw[3] = {GAUSS_W0, GAUSS_W1, GAUSS_W0};
-  double Wn[4];
+  double Wn[NC];
   const size_t cells = (size_t)nx * ny, c = (size_t)j * nx + i;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < NC; ++q) {
     double fl = 0.0, fr = 0.0, gb = 0.0, gt = 0.0, wl = 0.0, wr = 0.0, wb = 0.0, wt = 0.0;
 #pragma unroll
     for (int g = 0; g < 3; ++g) {
-      const size_t ox = ((size_t)(g * 4 + q) * ny + j) * (nx + 1) + i;
-      const size_t oy = ((size_t)(g * 4 + q) * (ny + 1) + j) * nx + i;
+      const size_t ox = ((size_t)(g * NC + q) * ny + j) * (nx + 1) + i;
+      const size_t oy = ((size_t)(g * NC + q) * (ny + 1) + j) * nx + i;
       fl += gw[g] * __ldcg(FX + ox);
       fr += gw[g] * __ldcg(FX + ox + 1);
       wl += gw[g] * __ldcg(WX + ox);
@@ -361,9 +366,9 @@ __device__ __forceinline__ double update2d_cell(const Params& P, Ctl* __restrict
     const double z = (__ldcg(WC + oc + (nx + 1) + 1) - __ldcg(WC + oc + (nx + 1)) - __ldcg(WC + oc + 1) + __ldcg(WC + oc)) / (P.dx * P.dy);
     Wn[q] = __ldcg(st + q * cells + c) - dt / P.dx * (fr - fl) - dt / P.dy * (gt - gb);
     out[q * cells + c] = Wn[q];
-    out[(4 + q) * cells + c] = (wr - wl) / P.dx;
-    out[(8 + q) * cells + c] = (wt - wb) / P.dy;
-    out[(12 + q) * cells + c] = z;
+    out[(NC + q) * cells + c] = (wr - wl) / P.dx;
+    out[(2 * NC + q) * cells + c] = (wt - wb) / P.dy;
+    out[(3 * NC + q) * cells + c] = z;
   }
   if (!cell_physical(P, Wn)) {
     atomicCAS(&ctl->err, ERR_NONE, ERR_NONPHYSICAL);

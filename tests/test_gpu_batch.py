@@ -73,7 +73,9 @@ def test_batch_2d_and_mixed_equals_solo():
     wls = [WL.riemann2d(n, WL.random_quadrants(s)) for s, n in zip((10, 11, 12), (24, 40, 70))]
     wls.append(WL.vortex(32))
     wls.append(WL.random_riemann1d(3, nx=200))
-    T = [0.02, 0.02, 0.02, 0.3, 0.02]
+    wls.append(WL.burgers2d_riemann(36))
+    wls.append(WL.burgers_sine(150))
+    T = [0.02, 0.02, 0.02, 0.3, 0.02, 0.1, 0.1]
     outs, per = batch_of(wls, T)
     for wl, t, o, st in zip(wls, T, outs, per):
         same(o, solo(wl, t), wl, st)
