@@ -33,6 +33,7 @@ class Problem(ctypes.Structure):
         ("linear", ctypes.c_int32),
         ("eps", ctypes.c_double),
         ("gam", ctypes.c_double * 3),
+        ("charwise", ctypes.c_int32),
     ]
 
 
@@ -73,7 +74,7 @@ def lib():
         L.orc_max_rate.restype = ctypes.c_double
         L.orc_step.argtypes = [pp, dp, dp, dp, dp, u8p, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
         L.orc_run.argtypes = [pp, dp, dp, dp, dp, u8p, ctypes.c_double, ctypes.c_double,
-                              ctypes.c_int64, dp]
+                              ctypes.c_int64, dp, ctypes.POINTER(ctypes.c_int32)]
         L.orc_step2d_cells.argtypes = [pp, dp, dp, dp, dp, u8p, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int32), dp]
         L.orc_run.restype = ctypes.c_int64
@@ -94,7 +95,7 @@ def _f64(a):
 
 
 def make_problem(dim, eq, nx, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, bc=(0, 0, 0, 0),
-                 inflow=None, linear=False, eps=1e-6, gam=GAMMA_LINEAR) -> Problem:
+                 inflow=None, linear=False, eps=1e-6, gam=GAMMA_LINEAR, charwise=False) -> Problem:
     P = Problem()
     P.dim, P.eq, P.nx, P.ny = dim, eq, nx, (ny if dim == 2 else 1)
     P.x0, P.y0 = x0, y0
@@ -111,6 +112,7 @@ def make_problem(dim, eq, nx, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, b
     P.eps = eps
     for k in range(3):
         P.gam[k] = gam[k]
+    P.charwise = 1 if charwise else 0
     return P
 
 
@@ -256,16 +258,28 @@ def features2d(P, state, t=0.0):
     return out
 
 
+class NonPhysical(RuntimeError):
+    """A step of run() left the physical range; state/steps/t are those before that step."""
+
+    def __init__(self, state, steps, t):
+        super().__init__(f"non-physical state after {steps} steps at t = {t}")
+        self.state, self.steps, self.t = state, steps, t
+
+
 def run(P, state, t_final, cfl, flag=None, max_steps=10 ** 9):
-    """Runs to t_final (CFL step size, last step shortened).  Returns (state, steps, t)."""
+    """Runs to t_final (CFL step size, last step shortened).  Returns (state, steps, t); raises
+    NonPhysical when a step leaves the physical range (that step is not kept)."""
     W, V = _f64(state["W"]).copy(), _f64(state["V"]).copy()
     Y = _f64(state["Y"]).copy() if P.dim == 2 else None
     Z = _f64(state["Z"]).copy() if P.dim == 2 else None
     fl, fp = _flag_ptr(flag)
     t = ctypes.c_double(0.0)
+    bad = ctypes.c_int32(0)
     n = lib().orc_run(ctypes.byref(P), _dp(W), _dp(V), _dp(Y), _dp(Z), fp, t_final, cfl,
-                      max_steps, ctypes.byref(t))
+                      max_steps, ctypes.byref(t), ctypes.byref(bad))
     out = {"W": W, "V": V}
     if P.dim == 2:
         out["Y"], out["Z"] = Y, Z
+    if bad.value:
+        raise NonPhysical(out, n, t.value)
     return out, n, t.value

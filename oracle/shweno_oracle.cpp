@@ -51,6 +51,7 @@ struct Problem {
   int32_t linear;        // 1: every reconstruction uses the linear weights
   double eps;            // epsilon in the nonlinear weights
   double gam[3];         // linear weights gamma_1..3 (Section 2.4)
+  int32_t charwise;      // 1: Euler reconstructions across a face in characteristic fields
 };
 
 int ncomp(const Problem& P) {
@@ -632,6 +633,39 @@ void recon_eval(const Problem& P, const double Wb[3], const double v[2], int non
 }
 
 // ----------------------------------------------------------------------------------------
+// Fields of the reconstruction across a face (an option; the paper reconstructs the conserved
+// variables).  Componentwise: R = L = identity.  Characteristic-wise (Euler, P.charwise = 1):
+// the stencil data of both sides are projected with the left eigenvectors L = R^{-1} of the
+// Jacobian along the face normal at W_ref, reconstructed field by field, and mapped back with R.
+// ----------------------------------------------------------------------------------------
+void basis_at(const Problem& P, int dir, const double* Wref, double* R, double* L) {
+  const int nc = ncomp(P);
+  if (!P.charwise || nc == 1) {
+    for (int a = 0; a < nc * nc; ++a) R[a] = L[a] = (a % (nc + 1) == 0) ? 1.0 : 0.0;
+    return;
+  }
+  double lam[4];
+  eigensystem(P, dir, Wref, lam, R);
+  invert(nc, R, L);
+}
+// W_ref = mean of the cell averages of cells (i0, j0) and (i1, j1) on the two sides.
+void face_basis(const Problem& P, int dir, const State& S, int i0, int j0, int i1, int j1,
+                double* R, double* L) {
+  const int nc = ncomp(P);
+  double Wref[4];
+  for (int q = 0; q < nc; ++q) Wref[q] = 0.5 * (fetch(S, 0, q, i0, j0) + fetch(S, 0, q, i1, j1));
+  basis_at(P, dir, Wref, R, L);
+}
+// out = M x for an nc x nc row-major matrix.
+void project(int nc, const double* M, const double* x, double* out) {
+  for (int a = 0; a < nc; ++a) {
+    double s = 0.0;
+    for (int b = 0; b < nc; ++b) s += M[a * nc + b] * x[b];
+    out[a] = s;
+  }
+}
+
+// ----------------------------------------------------------------------------------------
 // One time step in 1D (Section 2; Section 4 Steps 1-5).
 // ----------------------------------------------------------------------------------------
 void step1d(const Problem& P, const State& S, double dt, double* Wn, double* Vn) {
@@ -641,14 +675,34 @@ void step1d(const Problem& P, const State& S, double dt, double* Wn, double* Vn)
   for (int fc = 0; fc <= N; ++fc) {  // face between cells fc-1 and fc
     Deriv dL[4], dR[4];
     std::memset(dL, 0, sizeof(dL)); std::memset(dR, 0, sizeof(dR));
-    for (int q = 0; q < nc; ++q) {
-      for (int side = 0; side < 2; ++side) {
-        int cell = fc - 1 + side;
-        double Wb[3] = {fetch(S, 0, q, cell - 1, 0), fetch(S, 0, q, cell, 0), fetch(S, 0, q, cell + 1, 0)};
-        double v[2] = {h * fetch(S, 1, q, cell - 1, 0), h * fetch(S, 1, q, cell + 1, 0)};
-        double d[5];
-        recon_eval(P, Wb, v, cell_flag(S, cell, 0), side == 0 ? 0.5 : -0.5, d);
-        for (int m = 0; m <= ORD; ++m) (side == 0 ? dL : dR)[q][m][0] = d[m] / std::pow(h, m);
+    // projection onto the fields in which each side is reconstructed: the identity
+    // (componentwise), or the left eigenvectors of F'(W_ref) at the mean of the two cells
+    double Rm[16], Lm[16];
+    face_basis(P, 0, S, fc - 1, 0, fc, 0, Rm, Lm);
+    for (int side = 0; side < 2; ++side) {
+      const int cell = fc - 1 + side;
+      double Wc[3][4], Vc[2][4];  // stencil data in the reconstruction fields
+      for (int r = 0; r < 3; ++r) {
+        double w[4];
+        for (int q = 0; q < nc; ++q) w[q] = fetch(S, 0, q, cell - 1 + r, 0);
+        project(nc, Lm, w, Wc[r]);
+      }
+      for (int r = 0; r < 2; ++r) {
+        double w[4];
+        for (int q = 0; q < nc; ++q) w[q] = h * fetch(S, 1, q, cell - 1 + 2 * r, 0);
+        project(nc, Lm, w, Vc[r]);
+      }
+      double dk[4][5];
+      for (int k = 0; k < nc; ++k) {
+        double Wb[3] = {Wc[0][k], Wc[1][k], Wc[2][k]};
+        double v[2] = {Vc[0][k], Vc[1][k]};
+        recon_eval(P, Wb, v, cell_flag(S, cell, 0), side == 0 ? 0.5 : -0.5, dk[k]);
+      }
+      for (int m = 0; m <= ORD; ++m) {
+        double a[4], b[4];
+        for (int k = 0; k < nc; ++k) a[k] = dk[k][m];
+        project(nc, Rm, a, b);
+        for (int q = 0; q < nc; ++q) (side == 0 ? dL : dR)[q][m][0] = b[q] / std::pow(h, m);
       }
     }
     double tc[4][5], F[4], Wend[4];
@@ -702,9 +756,25 @@ void xpass(const State& S, int i, int j, double xi, double out[2][4][5]) {
 // a+1); k is the derivative order along the face.  The weights of each side come from the
 // k = 0 data and serve every k (reading of Section 3.2 with the remark ending Section 2.1.2).
 // Returns d[q][p][k]: p-th normal derivative of the k-th tangential derivative.
-void second_pass(const Problem& P, double hn, const double line[4][2][4][5], int flagL, int flagR,
-                 Deriv* dL, Deriv* dR) {
+void second_pass(const Problem& P, int dir, double hn, const double line_in[4][2][4][5], int flagL,
+                 int flagR, Deriv* dL_out, Deriv* dR_out) {
   const int nc = ncomp(P);
+  // reconstruction fields: W_ref is the mean of the order-0 first-pass values (set 0) of the
+  // two cells next to the face at this point
+  double Rm[16], Lm[16], Wref[4];
+  for (int q = 0; q < nc; ++q) Wref[q] = 0.5 * (line_in[1][0][q][0] + line_in[2][0][q][0]);
+  basis_at(P, dir, Wref, Rm, Lm);
+  double line[4][2][4][5];
+  for (int c = 0; c < 4; ++c)
+    for (int set = 0; set < 2; ++set)
+      for (int k = 0; k <= ORD; ++k) {
+        double x[4], y[4];
+        for (int q = 0; q < nc; ++q) x[q] = line_in[c][set][q][k];
+        project(nc, Lm, x, y);
+        for (int q = 0; q < nc; ++q) line[c][set][q][k] = y[q];
+      }
+  Deriv dL[4], dR[4];
+  std::memset(dL, 0, sizeof(dL)); std::memset(dR, 0, sizeof(dR));
   for (int side = 0; side < 2; ++side) {
     int base = side;  // stencil cells base..base+2; the reconstructed cell is base+1
     double xi = side == 0 ? 0.5 : -0.5;
@@ -725,6 +795,17 @@ void second_pass(const Problem& P, double hn, const double line[4][2][4][5], int
         for (int p = 0; p + k <= ORD; ++p) (side == 0 ? dL : dR)[q][p][k] = d[p] / std::pow(hn, p);
       }
     }
+  }
+  for (int side = 0; side < 2; ++side) {
+    const Deriv* in = side == 0 ? dL : dR;
+    Deriv* out = side == 0 ? dL_out : dR_out;
+    for (int p = 0; p <= ORD; ++p)
+      for (int k = 0; p + k <= ORD; ++k) {
+        double x[4], y[4];
+        for (int q = 0; q < nc; ++q) x[q] = in[q][p][k];
+        project(nc, Rm, x, y);
+        for (int q = 0; q < nc; ++q) out[q][p][k] = y[q];
+      }
   }
 }
 // Swaps the roles of the indices of a derivative table so that [m][n] is always
@@ -750,7 +831,7 @@ void xface(const State& S, int i, int j, double dt, double* Fs, double* Ws) {
     double line[4][2][4][5];
     for (int c = 0; c < 4; ++c) ypass(S, i - 1 + c, j, gs[g], line[c]);
     Deriv a[4], b[4], dL[4], dR[4];
-    second_pass(P, P.dx, line, cell_flag(S, i, j), cell_flag(S, i + 1, j), a, b);
+    second_pass(P, 0, P.dx, line, cell_flag(S, i, j), cell_flag(S, i + 1, j), a, b);
     to_xy(nc, a, 1, dL); to_xy(nc, b, 1, dR);
     double tc[4][5], F[4], We[4];
     grp_point(P, 0, dL, dR, tc);
@@ -769,7 +850,7 @@ void yface(const State& S, int i, int j, double dt, double* Gs, double* Ws) {
     double line[4][2][4][5];
     for (int c = 0; c < 4; ++c) xpass(S, i, j - 1 + c, gs[g], line[c]);
     Deriv a[4], b[4], dB[4], dT[4];
-    second_pass(P, P.dy, line, cell_flag(S, i, j), cell_flag(S, i, j + 1), a, b);
+    second_pass(P, 1, P.dy, line, cell_flag(S, i, j), cell_flag(S, i, j + 1), a, b);
     to_xy(nc, a, 0, dB); to_xy(nc, b, 0, dT);
     double tc[4][5], G[4], We[4];
     grp_point(P, 1, dB, dT, tc);
@@ -795,7 +876,7 @@ void corner(const State& S, int i, int j, double dt, double* We) {
   int fL = cell_flag(S, i, j) | cell_flag(S, i, j + 1);
   int fR = cell_flag(S, i + 1, j) | cell_flag(S, i + 1, j + 1);
   Deriv a[4], b[4], dL[4], dR[4];
-  second_pass(P, P.dx, line, fL, fR, a, b);
+  second_pass(P, 0, P.dx, line, fL, fR, a, b);
   to_xy(nc, a, 1, dL); to_xy(nc, b, 1, dR);
   double tc[4][5];
   grp_point(P, 0, dL, dR, tc);
@@ -1107,18 +1188,41 @@ void orc_step2d_window(const orc_problem* P, const double* W, const double* V, c
 
 // Runs to t_final with dt = cfl / max_rate, the last step shortened to land on t_final.
 // State arrays are updated in place.  Returns the number of steps; max_steps bounds the loop
-// (a negative return means it was hit).
+// (a negative return means it was hit).  A step that leaves the physical range in some cell
+// (Euler: rho <= 0, p <= 0 or a non-finite value; Burgers: a non-finite value) is not kept:
+// the run stops at the state before it and *nonphysical is set to 1 (0 otherwise).
 int64_t orc_run(const orc_problem* P, double* W, double* V, double* Y, double* Z,
-                const uint8_t* flag, double t_final, double cfl, int64_t max_steps, double* t_out) {
+                const uint8_t* flag, double t_final, double cfl, int64_t max_steps, double* t_out,
+                int32_t* nonphysical) {
   const size_t n = (size_t)ncomp(*P) * P->nx * (P->dim == 2 ? P->ny : 1);
+  const size_t cells = (size_t)P->nx * (P->dim == 2 ? P->ny : 1);
   std::vector<double> a(n), b(n), c(n), d(n);
   double t = 0.0;
   int64_t steps = 0;
+  *nonphysical = 0;
   while (t < t_final) {
     if (steps >= max_steps) { *t_out = t; return -steps; }
     double dt = cfl / max_rate(*P, W);
     if (dt > t_final - t) dt = t_final - t;
     orc_step(P, W, V, Y, Z, flag, t, dt, a.data(), b.data(), c.data(), d.data());
+    for (size_t k = 0; k < cells; ++k) {
+      bool ok;
+      if (P->eq == EQ_BURGERS) {
+        ok = std::isfinite(a[k]);
+      } else {
+        const int nc = ncomp(*P);
+        const double rho = a[k];
+        double m2 = 0.0;
+        for (int q = 1; q < nc - 1; ++q) m2 += a[q * cells + k] * a[q * cells + k];
+        const double p = (P->gamma - 1.0) * (a[(nc - 1) * cells + k] - 0.5 * m2 / rho);
+        ok = rho > 0.0 && p > 0.0 && std::isfinite(rho) && std::isfinite(p);
+      }
+      if (!ok) {
+        *nonphysical = 1;
+        *t_out = t;
+        return steps;
+      }
+    }
     std::memcpy(W, a.data(), n * sizeof(double));
     std::memcpy(V, b.data(), n * sizeof(double));
     if (P->dim == 2) {

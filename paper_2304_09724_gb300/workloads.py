@@ -70,6 +70,67 @@ def project_1d(fun, x0, x1, nx, nq=6, eps_edge=0.0):
     return np.ascontiguousarray(W), np.ascontiguousarray(V)
 
 
+def project_pieces_1d(pieces, x0, x1, nx, nq=6):
+    """Cell and derivative averages of piecewise-smooth data: pieces = [(a, b, fun)] covering
+    [x0, x1] in order.  Each cell's average integrates every piece over its part of the cell
+    (nq-point Gauss on that part), so a jump inside a cell is exact; an edge value is the limit
+    from inside the cell."""
+    dx = (x1 - x0) / nx
+    xl = x0 + np.arange(nx) * dx
+    xr = xl + dx
+    s, w = _gauss(nq)
+    W = 0.0
+    for a, b, f in pieces:
+        lo, hi = np.maximum(xl, a), np.minimum(xr, b)
+        ln = np.maximum(hi - lo, 0.0)
+        mid = 0.5 * (lo + hi)
+        W = W + sum(wk * f(mid + sk * ln) for sk, wk in zip(s, w)) * (ln / dx)
+    right_edge = 0.0
+    left_edge = 0.0
+    for a, b, f in pieces:
+        right_edge = right_edge + np.where((a < xr) & (xr <= b), f(xr), 0.0)
+        left_edge = left_edge + np.where((a <= xl) & (xl < b), f(xl), 0.0)
+    V = (right_edge - left_edge) / dx
+    return np.ascontiguousarray(W), np.ascontiguousarray(V)
+
+
+def _prim_piece(rho, u, p):
+    """fun(x) -> conserved (rho, rho u, E) of primitive data given as numbers or callables."""
+    def f(x):
+        ev = lambda v: v(x) if callable(v) else np.full_like(x, v, dtype=np.float64)
+        return euler_conserved(ev(rho), ev(u), ev(p))
+    return f
+
+
+def shu_osher(nx=400, t_final=1.8, cfl=0.6):
+    """Example 5.4: a Mach 3 shock meeting the density wave 1 + 0.2 sin(5x) on (-5, 5),
+    inflow/outflow sides (the states at the ends do not change before T)."""
+    pieces = [(-5.0, -4.0, _prim_piece(3.857143, 2.629369, 10.333333)),
+              (-4.0, 5.0, _prim_piece(lambda x: 1.0 + 0.2 * np.sin(5.0 * x), 0.0, 1.0))]
+    W, V = project_pieces_1d(pieces, -5.0, 5.0, nx)
+    return Workload("shu_osher", 1, EULER, nx, 1, (-5.0, 5.0, 0.0, 1.0), (OUTFLOW, OUTFLOW, 0, 0),
+                    t_final, cfl, {"W": W, "V": V}, shocked=True)
+
+
+def turbulence_interaction(nx=1500, t_final=5.0, cfl=0.6):
+    """Example 5.5: a shock meeting the density wave 1 + 0.1 sin(20 pi x) on (-5, 5)."""
+    pieces = [(-5.0, -4.5, _prim_piece(1.515695, 0.523346, 1.80500)),
+              (-4.5, 5.0, _prim_piece(lambda x: 1.0 + 0.1 * np.sin(20.0 * np.pi * x), 0.0, 1.0))]
+    W, V = project_pieces_1d(pieces, -5.0, 5.0, nx)
+    return Workload("turbulence_interaction", 1, EULER, nx, 1, (-5.0, 5.0, 0.0, 1.0),
+                    (OUTFLOW, OUTFLOW, 0, 0), t_final, cfl, {"W": W, "V": V}, shocked=True)
+
+
+def blast_waves(nx=800, t_final=0.038, cfl=0.6):
+    """Example 5.6 (Woodward-Colella): pressures 1000 / 0.01 / 100 split at 0.1 and 0.9 on
+    (0, 1), rho = 1, u = 0, reflective walls at both ends."""
+    pieces = [(0.0, 0.1, _prim_piece(1.0, 0.0, 1000.0)), (0.1, 0.9, _prim_piece(1.0, 0.0, 0.01)),
+              (0.9, 1.0, _prim_piece(1.0, 0.0, 100.0))]
+    W, V = project_pieces_1d(pieces, 0.0, 1.0, nx)
+    return Workload("blast_waves", 1, EULER, nx, 1, (0.0, 1.0, 0.0, 1.0), (REFLECTIVE, REFLECTIVE, 0, 0),
+                    t_final, cfl, {"W": W, "V": V}, shocked=True)
+
+
 def project_2d(fun, x0, x1, y0, y1, nx, ny, nq=6, eps_edge=0.0):
     """W, V, Y, Z of fun(x, y) -> [nc, ...] by nq-point Gauss rules (tensor rule for W, edge rule
     for V and Y, corners for Z).  eps_edge > 0 takes edge values just inside the cell, which is
