@@ -756,13 +756,12 @@ void xpass(const State& S, int i, int j, double xi, double out[2][4][5]) {
 // a+1); k is the derivative order along the face.  The weights of each side come from the
 // k = 0 data and serve every k (reading of Section 3.2 with the remark ending Section 2.1.2).
 // Returns d[q][p][k]: p-th normal derivative of the k-th tangential derivative.
+// Wref: state whose flux-Jacobian eigenvectors along dir span the reconstruction fields (used
+// when P.charwise is set).
 void second_pass(const Problem& P, int dir, double hn, const double line_in[4][2][4][5], int flagL,
-                 int flagR, Deriv* dL_out, Deriv* dR_out) {
+                 int flagR, const double* Wref, Deriv* dL_out, Deriv* dR_out) {
   const int nc = ncomp(P);
-  // reconstruction fields: W_ref is the mean of the order-0 first-pass values (set 0) of the
-  // two cells next to the face at this point
-  double Rm[16], Lm[16], Wref[4];
-  for (int q = 0; q < nc; ++q) Wref[q] = 0.5 * (line_in[1][0][q][0] + line_in[2][0][q][0]);
+  double Rm[16], Lm[16];
   basis_at(P, dir, Wref, Rm, Lm);
   double line[4][2][4][5];
   for (int c = 0; c < 4; ++c)
@@ -831,7 +830,9 @@ void xface(const State& S, int i, int j, double dt, double* Fs, double* Ws) {
     double line[4][2][4][5];
     for (int c = 0; c < 4; ++c) ypass(S, i - 1 + c, j, gs[g], line[c]);
     Deriv a[4], b[4], dL[4], dR[4];
-    second_pass(P, 0, P.dx, line, cell_flag(S, i, j), cell_flag(S, i + 1, j), a, b);
+    double Wref[4];
+    for (int q = 0; q < nc; ++q) Wref[q] = 0.5 * (fetch(S, 0, q, i, j) + fetch(S, 0, q, i + 1, j));
+    second_pass(P, 0, P.dx, line, cell_flag(S, i, j), cell_flag(S, i + 1, j), Wref, a, b);
     to_xy(nc, a, 1, dL); to_xy(nc, b, 1, dR);
     double tc[4][5], F[4], We[4];
     grp_point(P, 0, dL, dR, tc);
@@ -850,7 +851,9 @@ void yface(const State& S, int i, int j, double dt, double* Gs, double* Ws) {
     double line[4][2][4][5];
     for (int c = 0; c < 4; ++c) xpass(S, i, j - 1 + c, gs[g], line[c]);
     Deriv a[4], b[4], dB[4], dT[4];
-    second_pass(P, 1, P.dy, line, cell_flag(S, i, j), cell_flag(S, i, j + 1), a, b);
+    double Wref[4];
+    for (int q = 0; q < nc; ++q) Wref[q] = 0.5 * (fetch(S, 0, q, i, j) + fetch(S, 0, q, i, j + 1));
+    second_pass(P, 1, P.dy, line, cell_flag(S, i, j), cell_flag(S, i, j + 1), Wref, a, b);
     to_xy(nc, a, 0, dB); to_xy(nc, b, 0, dT);
     double tc[4][5], G[4], We[4];
     grp_point(P, 1, dB, dT, tc);
@@ -876,7 +879,11 @@ void corner(const State& S, int i, int j, double dt, double* We) {
   int fL = cell_flag(S, i, j) | cell_flag(S, i, j + 1);
   int fR = cell_flag(S, i + 1, j) | cell_flag(S, i + 1, j + 1);
   Deriv a[4], b[4], dL[4], dR[4];
-  second_pass(P, 0, P.dx, line, fL, fR, a, b);
+  double Wref[4];
+  for (int q = 0; q < nc; ++q)
+    Wref[q] = 0.25 * (fetch(S, 0, q, i, j) + fetch(S, 0, q, i + 1, j) + fetch(S, 0, q, i, j + 1) +
+                      fetch(S, 0, q, i + 1, j + 1));
+  second_pass(P, 0, P.dx, line, fL, fR, Wref, a, b);
   to_xy(nc, a, 1, dL); to_xy(nc, b, 1, dR);
   double tc[4][5];
   grp_point(P, 0, dL, dR, tc);
