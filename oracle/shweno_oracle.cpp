@@ -259,7 +259,12 @@ double burgers_godunov(double uL, double uR) {
 // Section 10.4): Davis wave-speed estimates S_L = min(uL-cL, uR-cR), S_R = max(uL+cL, uR+cR),
 // contact speed S*, star states U*_K = rho_K (S_K-u_K)/(S_K-S*) (1, S*, v_K,
 // E_K/rho_K + (S*-u_K)(S* + p_K/(rho_K (S_K-u_K)))) with the normal and tangential velocity
-// placed by the face direction.  A wave of speed exactly 0 hands over its left-hand state.
+// placed by the face direction.  A wave of speed exactly 0 hands over its left-hand state; a
+// contact whose speed is within STANDING_WAVE_TOL x (larger sound speed) of zero counts as
+// standing (the normal velocity of a gas at rest is zero in exact arithmetic, and rounding must
+// not pick the star state).
+const double STANDING_WAVE_TOL = 1e-12;
+
 void hllc_state(const Problem& P, int dir, const double* WL, const double* WR, double* out) {
   const double g = P.gamma;
   const int nc = ncomp(P);
@@ -293,7 +298,7 @@ void hllc_state(const Problem& P, int dir, const double* WL, const double* WR, d
     }
   };
   if (0.0 <= SL) { for (int q = 0; q < nc; ++q) out[q] = WL[q]; }
-  else if (0.0 <= Ss) star(WL, rL, uL, tL, pL, SL, out);
+  else if (-STANDING_WAVE_TOL * std::fmax(cL, cR) <= Ss) star(WL, rL, uL, tL, pL, SL, out);
   else if (0.0 <= SR) star(WR, rR, uR, tR, pR, SR, out);
   else { for (int q = 0; q < nc; ++q) out[q] = WR[q]; }
 }
@@ -307,8 +312,6 @@ void hllc_state(const Problem& P, int dir, const double* WL, const double* WR, d
 // (the normal velocity at a reflective wall) is not decided by rounding.
 // Right eigenvectors of the Euler Jacobian (Toro, Section 3.2), L = R^{-1} by elimination.
 // ----------------------------------------------------------------------------------------
-const double STANDING_WAVE_TOL = 1e-12;
-
 void eigensystem(const Problem& P, int dir, const double* W, double* lam, double* R) {
   const int nc = ncomp(P);
   if (P.eq == EQ_BURGERS) { lam[0] = W[0]; R[0] = 1.0; return; }

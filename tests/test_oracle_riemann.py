@@ -68,6 +68,27 @@ def test_hllc_resolves_stationary_contact_and_shear():
     np.testing.assert_allclose(O.hllc(P, 0, UL, UR), UR, rtol=1e-13)
 
 
+@pytest.mark.parametrize("dE", [-1, 1])
+def test_hllc_contact_at_rest_within_rounding_is_standing(dE):
+    """A gas at rest whose two sides differ in pressure by one rounding step still counts as a
+    standing contact: the left star state, the same whichever way the rounding went (reading of
+    the leading term at a contact of speed zero)."""
+    P = prob(1)
+    UL = cons(1.0, 0.0, 1.0)
+    UR = cons(0.25, 0.0, 1.0)
+    exact = O.hllc(P, 0, UL, UR)
+    np.testing.assert_allclose(exact, UL, rtol=1e-14)
+    URp = UR.copy()
+    URp[2] = np.nextafter(UR[2], UR[2] + dE)
+    got = O.hllc(P, 0, UL, URp)
+    np.testing.assert_allclose(got, UL, rtol=1e-14, atol=1e-15)
+    # a contact moving at a small but resolved speed still goes by its sign
+    URm = cons(0.25, 0.0, 1.0 + 1e-6 * dE)
+    ULm = cons(1.0, 0.0, 1.0)
+    s = O.hllc(P, 0, ULm, URm)
+    assert abs(s[0] - 1.0) < 1e-5 if dE < 0 else abs(s[0] - 0.25) < 1e-5
+
+
 def test_hllc_y_direction_is_x_direction_rotated():
     P = prob(2)
     rng = np.random.default_rng(2)
