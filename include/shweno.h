@@ -80,12 +80,19 @@ typedef struct {
 } shweno_bc;
 
 /* Reconstruction options.  Defaults (opts == NULL): nonlinear weights everywhere,
- * eps = 1e-6, linear weights gamma = (0.994, 0.003, 0.003) (Section 2.4). */
+ * eps = 1e-6, linear weights gamma = (0.994, 0.003, 0.003) (Section 2.4), componentwise
+ * reconstruction of the conserved variables (the paper's). */
 typedef struct {
   int32_t flag_mode;  /* 0: nonlinear weights in every cell; 1: linear weights in every cell;
                          2: per-cell troubled flags (shweno_set_flags) */
   double eps;         /* epsilon of the nonlinear weights */
   double gam[3];      /* linear weights, positive, summing to 1 */
+  int32_t charwise;   /* not in the paper.  0: componentwise; 1 (Euler): each reconstruction
+                         across a face runs in the characteristic fields of the flux Jacobian
+                         along the face normal at the mean of the two adjacent states (1D: the
+                         two cell averages; 2D: the two order-0 values of the pass along the
+                         face at that point), projected with the left eigenvectors and mapped
+                         back with the right ones; no effect for Burgers */
 } shweno_opts;
 
 typedef struct shweno_handle shweno_handle;
@@ -218,7 +225,10 @@ shweno_status shweno_get_flags(shweno_handle* h, uint8_t* out, int on_device);
  * the batch and must not be used on their own while a batch run is in flight. */
 typedef struct shweno_batch shweno_batch;
 
-/* Groups n handles.  cuda_stream: stream of the batch's work (NULL: its own). */
+/* Groups n handles.  cuda_stream: stream of the batch's work (NULL: its own).
+ * Errors: INVALID (null or bad handle; a 2D handle created with charwise = 1, whose
+ * characteristic face items the persistent kernel does not carry), STATE (a per-cell-flag
+ * handle without flags or flag network). */
 shweno_status shweno_batch_create(shweno_handle* const* hs, int n, void* cuda_stream,
                                   shweno_batch** out);
 

@@ -177,11 +177,11 @@ __device__ void do_item(const BatchProblem& B, int kind, long long idx, unsigned
         const int row = r < 3 * P.ny ? r % P.ny : r - 3 * P.ny;
         const int f0 = seg * SEG;
         if (P.ncomp == 1) {
-          if (flags) xface_item<1, true>(P, sv, B.S.ycoef, B.flag, B.S.FX, B.S.WX, B.S.WC, f0, row, slice, smem);
-          else xface_item<1, false>(P, sv, B.S.ycoef, B.flag, B.S.FX, B.S.WX, B.S.WC, f0, row, slice, smem);
+          if (flags) xface_item<1, true>(P, sv, sv.odd ? B.s1 : B.s0, B.S.ycoef, B.flag, B.S.FX, B.S.WX, B.S.WC, f0, row, slice, smem);
+          else xface_item<1, false>(P, sv, sv.odd ? B.s1 : B.s0, B.S.ycoef, B.flag, B.S.FX, B.S.WX, B.S.WC, f0, row, slice, smem);
         } else {
-          if (flags) xface_item<4, true>(P, sv, B.S.ycoef, B.flag, B.S.FX, B.S.WX, B.S.WC, f0, row, slice, smem);
-          else xface_item<4, false>(P, sv, B.S.ycoef, B.flag, B.S.FX, B.S.WX, B.S.WC, f0, row, slice, smem);
+          if (flags) xface_item<4, true>(P, sv, sv.odd ? B.s1 : B.s0, B.S.ycoef, B.flag, B.S.FX, B.S.WX, B.S.WC, f0, row, slice, smem);
+          else xface_item<4, false>(P, sv, sv.odd ? B.s1 : B.s0, B.S.ycoef, B.flag, B.S.FX, B.S.WX, B.S.WC, f0, row, slice, smem);
         }
       } else {
         const long long k = idx - B.nxitems;
@@ -189,11 +189,11 @@ __device__ void do_item(const BatchProblem& B, int kind, long long idx, unsigned
         const int slice = r / P.nx, col = r % P.nx;
         const int f0 = seg * SEG;
         if (P.ncomp == 1) {
-          if (flags) yface_item<1, true>(P, sv, B.S.xcoef, B.flag, B.S.FY, B.S.WY, f0, col, slice, smem);
-          else yface_item<1, false>(P, sv, B.S.xcoef, B.flag, B.S.FY, B.S.WY, f0, col, slice, smem);
+          if (flags) yface_item<1, true>(P, sv, sv.odd ? B.s1 : B.s0, B.S.xcoef, B.flag, B.S.FY, B.S.WY, f0, col, slice, smem);
+          else yface_item<1, false>(P, sv, sv.odd ? B.s1 : B.s0, B.S.xcoef, B.flag, B.S.FY, B.S.WY, f0, col, slice, smem);
         } else {
-          if (flags) yface_item<4, true>(P, sv, B.S.xcoef, B.flag, B.S.FY, B.S.WY, f0, col, slice, smem);
-          else yface_item<4, false>(P, sv, B.S.xcoef, B.flag, B.S.FY, B.S.WY, f0, col, slice, smem);
+          if (flags) yface_item<4, true>(P, sv, sv.odd ? B.s1 : B.s0, B.S.xcoef, B.flag, B.S.FY, B.S.WY, f0, col, slice, smem);
+          else yface_item<4, false>(P, sv, sv.odd ? B.s1 : B.s0, B.S.xcoef, B.flag, B.S.FY, B.S.WY, f0, col, slice, smem);
         }
       }
       break;
@@ -434,6 +434,8 @@ shweno_status shweno_batch_create(shweno_handle* const* hs, int n, void* cuda_st
   size_t cap_need = 0;
   for (int p = 0; p < n; ++p) {
     if (!hs[p] || !handle_view(hs[p], &b->views[p])) { delete b; return SHWENO_E_INVALID; }
+    // the persistent kernel carries the componentwise 2D face items only
+    if (b->views[p].P.dim == 2 && b->views[p].P.charwise) { delete b; return SHWENO_E_INVALID; }
     if (b->views[p].P.flag_mode == FLAG_PER_CELL && !b->views[p].flags && !b->views[p].learned) {
       delete b;
       return SHWENO_E_STATE;

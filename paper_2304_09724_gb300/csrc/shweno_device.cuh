@@ -27,6 +27,7 @@ struct Params {
   double eps;             // epsilon of the nonlinear weights
   double gam[3];          // linear weights
   int32_t flag_mode;      // FLAG_*
+  int32_t charwise;       // 1: Euler reconstructions across a face in characteristic fields
   // Cauchy-Kovalevskaya scale factors (m+1)/((k+1) dx) and (n+1)/((k+1) dy), set by the host
   double ckx[5][4], cky[5][4];
   double igam[3];  // 1 / gam, set by the host
@@ -279,7 +280,8 @@ __device__ __forceinline__ void hllc_state(const double* WL, const double* WR, d
     for (int q = 0; q < NC; ++q) out[q] = WR[q];
     return;
   }
-  const bool left = 0.0 <= Ss;
+  // a contact within rounding of standing (|S*| <= 1e-12 c) hands over the left star state
+  const bool left = -1e-12 * fmax(L.c, R.c) <= Ss;
   const double* W = left ? WL : WR;
   const Prim& K = left ? L : R;
   const double S = left ? SL : SR, un = left ? uL : uR, mK = left ? mL : mR;
@@ -330,6 +332,52 @@ __device__ __forceinline__ void phys_flux(const double* W, double g, int dir, do
 // evaluated as d* = base + sum_k s_k (l_k . (dL - dR)) r_k over the few waves that carry a
 // nonzero s_k: base = dR with s = H, or base = dL with s = H - 1, whichever needs fewer waves
 // (subsonic flow needs one acoustic wave).
+// Eigen-decomposition of the Euler flux Jacobian along dir (0: x, 1: y) at the primitive state
+// P (NC = 3: 1D, 4: 2D): r[k] = k-th right eigenvector, l[k] = k-th left eigenvector (rows of
+// R^{-1}), lam[k] = its speed; waves ordered u-c, entropy, (shear), u+c.
+template <int NC>
+__device__ __forceinline__ void euler_eigvecs(const Prim& P, double g, int dir, double r[NC][NC],
+                                              double l[NC][NC], double lam[NC]) {
+  const double un = dir == 0 ? P.u : P.v;
+  const double ut = dir == 0 ? P.v : P.u;
+  const double ic = 1.0 / P.c;
+  const double b1 = (g - 1.0) * ic * ic;
+  const double q2 = P.u * P.u + P.v * P.v;
+  const double b2 = 0.5 * b1 * q2;
+  lam[0] = un - P.c;
+  lam[NC - 1] = un + P.c;
+  const int in = 1 + dir;        // normal momentum slot
+  const int it = NC == 4 ? 2 - dir : -1;  // tangential momentum slot
+  // acoustic waves
+  for (int side = 0; side < 2; ++side) {
+    const int k = side == 0 ? 0 : NC - 1;
+    const double sg = side == 0 ? -1.0 : 1.0;
+    r[k][0] = 1.0;
+    r[k][in] = un + sg * P.c;
+    if (NC == 4) r[k][it] = ut;
+    r[k][NC - 1] = P.H + sg * un * P.c;
+    l[k][0] = 0.5 * (b2 - sg * un * ic);
+    l[k][in] = 0.5 * (-b1 * (dir == 0 ? P.u : P.v) + sg * ic);
+    if (NC == 4) l[k][it] = -0.5 * b1 * ut;
+    l[k][NC - 1] = 0.5 * b1;
+  }
+  // entropy wave
+  r[1][0] = 1.0;
+  r[1][in] = un;
+  if (NC == 4) r[1][it] = ut;
+  r[1][NC - 1] = 0.5 * q2;
+  l[1][0] = 1.0 - b2;
+  l[1][in] = b1 * un;
+  if (NC == 4) l[1][it] = b1 * ut;
+  l[1][NC - 1] = -b1;
+  lam[1] = un;
+  if (NC == 4) {  // shear wave
+    r[2][0] = 0.0; r[2][in] = 0.0; r[2][it] = 1.0; r[2][3] = ut;
+    l[2][0] = -ut; l[2][in] = 0.0; l[2][it] = 1.0; l[2][3] = 0.0;
+    lam[2] = un;
+  }
+}
+
 template <int NC>
 struct Upwinder {
   double r[NC][NC];  // r[k] = k-th right eigenvector
@@ -345,45 +393,8 @@ struct Upwinder {
       tol = 1e-12 * burgers_scale;
     } else {
       const Prim P = euler_prim(Ws, NC, g);
-      const double un = dir == 0 ? P.u : P.v;
-      const double ut = dir == 0 ? P.v : P.u;
-      const double ic = 1.0 / P.c;
       tol = 1e-12 * P.c;
-      const double b1 = (g - 1.0) * ic * ic;
-      const double q2 = P.u * P.u + P.v * P.v;
-      const double b2 = 0.5 * b1 * q2;
-      lam[0] = un - P.c;
-      lam[NC - 1] = un + P.c;
-      const int in = 1 + dir;        // normal momentum slot
-      const int it = NC == 4 ? 2 - dir : -1;  // tangential momentum slot
-      // acoustic waves
-      for (int side = 0; side < 2; ++side) {
-        const int k = side == 0 ? 0 : NC - 1;
-        const double sg = side == 0 ? -1.0 : 1.0;
-        r[k][0] = 1.0;
-        r[k][in] = un + sg * P.c;
-        if (NC == 4) r[k][it] = ut;
-        r[k][NC - 1] = P.H + sg * un * P.c;
-        l[k][0] = 0.5 * (b2 - sg * un * ic);
-        l[k][in] = 0.5 * (-b1 * (dir == 0 ? P.u : P.v) + sg * ic);
-        if (NC == 4) l[k][it] = -0.5 * b1 * ut;
-        l[k][NC - 1] = 0.5 * b1;
-      }
-      // entropy wave
-      r[1][0] = 1.0;
-      r[1][in] = un;
-      if (NC == 4) r[1][it] = ut;
-      r[1][NC - 1] = 0.5 * q2;
-      l[1][0] = 1.0 - b2;
-      l[1][in] = b1 * un;
-      if (NC == 4) l[1][it] = b1 * ut;
-      l[1][NC - 1] = -b1;
-      lam[1] = un;
-      if (NC == 4) {  // shear wave
-        r[2][0] = 0.0; r[2][in] = 0.0; r[2][it] = 1.0; r[2][3] = ut;
-        l[2][0] = -ut; l[2][in] = 0.0; l[2][it] = 1.0; l[2][3] = 0.0;
-        lam[2] = un;
-      }
+      euler_eigvecs<NC>(P, g, dir, r, l, lam);
     }
     int npos = 0, nneg = 0;
     for (int k = 0; k < NC; ++k) {
@@ -417,6 +428,38 @@ struct Upwinder {
 #pragma unroll
         for (int q = 0; q < NC; ++q) out[q] += a * r[k][q];
       }
+    }
+  }
+};
+
+// Basis of the characteristic-wise reconstruction across a face with normal dir: the
+// eigenvectors of the Euler flux Jacobian at Wref (conserved), the mean of the two states
+// next to the face.  Stencil data are projected with L (v -> L v), reconstructed field by
+// field, and mapped back with R (x -> R x).
+template <int NC>
+struct CharBasis {
+  double r[NC][NC];  // r[k] = k-th right eigenvector: physical = sum_k x_k r[k]
+  double l[NC][NC];  // l[k] = k-th left eigenvector: field k = l[k] . physical
+  __device__ __forceinline__ void setup(const double* Wref, double g, int dir) {
+    double lam[NC];
+    euler_eigvecs<NC>(euler_prim(Wref, NC, g), g, dir, r, l, lam);
+  }
+  __device__ __forceinline__ void to_fields(const double* v, double* out) const {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      double a = 0.0;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) a = fma(l[k][q], v[q], a);
+      out[k] = a;
+    }
+  }
+  __device__ __forceinline__ void to_physical(const double* x, double* out) const {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      double a = 0.0;
+#pragma unroll
+      for (int k = 0; k < NC; ++k) a = fma(r[k][q], x[k], a);
+      out[q] = a;
     }
   }
 };

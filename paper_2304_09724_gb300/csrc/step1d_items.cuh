@@ -16,26 +16,75 @@ __device__ __forceinline__ void face1d_point(const Params& P, const double* st,
   const double g = P.gamma;
   double a[NC][25], dR[NC][25];
   double WL0[NC], WR0[NC];
+  bool done = false;
+  if constexpr (NC > 1) if (P.charwise) {
+    // characteristic fields of F'(W_ref), W_ref = mean of the two cells next to the face
+    double Wref[NC];
 #pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    const int cell = f - 1 + side;
-    const int nonlinear = cell_flag(P, flag, cell, 0);
-    const double xi0 = side == 0 ? 0.5 : -0.5;
+    for (int q = 0; q < NC; ++q) Wref[q] = 0.5 * (fetch(P, st, 0, q, f - 1, 0, t) + fetch(P, st, 0, q, f, 0, t));
+    CharBasis<NC> B;
+    B.setup(Wref, g, 0);
 #pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      const double Wm = fetch(P, st, 0, q, cell - 1, 0, t);
-      const double W0 = fetch(P, st, 0, q, cell, 0, t);
-      const double Wp = fetch(P, st, 0, q, cell + 1, 0, t);
-      const double vm = P.dx * fetch(P, st, 1, q, cell - 1, 0, t);
-      const double vp = P.dx * fetch(P, st, 1, q, cell + 1, 0, t);
-      double c[5], e[5];
-      p1_coeffs(Wm, W0, Wp, vm, vp, c);
-      const Mix mx = shweno_mix(P, Wm, W0, Wp, c, nonlinear);
-      mix_coeffs(mx, Wm, W0, Wp, c, e);
-      taylor_shift(e, xi0, 4);
+    for (int side = 0; side < 2; ++side) {
+      const int cell = f - 1 + side;
+      const int nonlinear = cell_flag(P, flag, cell, 0);
+      const double xi0 = side == 0 ? 0.5 : -0.5;
+      double d[5][NC], x[5][NC];  // stencil data W-, W0, W+, h V-, h V+: physical, then fields
 #pragma unroll
-      for (int m = 0; m < 5; ++m) (side == 0 ? a : dR)[q][m * 5] = e[m];
-      (side == 0 ? WL0 : WR0)[q] = e[0];
+      for (int q = 0; q < NC; ++q) {
+        d[0][q] = fetch(P, st, 0, q, cell - 1, 0, t);
+        d[1][q] = fetch(P, st, 0, q, cell, 0, t);
+        d[2][q] = fetch(P, st, 0, q, cell + 1, 0, t);
+        d[3][q] = P.dx * fetch(P, st, 1, q, cell - 1, 0, t);
+        d[4][q] = P.dx * fetch(P, st, 1, q, cell + 1, 0, t);
+      }
+#pragma unroll
+      for (int r = 0; r < 5; ++r) B.to_fields(d[r], x[r]);
+      double e[NC][5];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        double c[5];
+        p1_coeffs(x[0][k], x[1][k], x[2][k], x[3][k], x[4][k], c);
+        const Mix mx = shweno_mix(P, x[0][k], x[1][k], x[2][k], c, nonlinear);
+        mix_coeffs(mx, x[0][k], x[1][k], x[2][k], c, e[k]);
+        taylor_shift(e[k], xi0, 4);
+      }
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        double xm[NC], ym[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) xm[k] = e[k][m];
+        B.to_physical(xm, ym);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) (side == 0 ? a : dR)[q][m * 5] = ym[q];
+      }
+#pragma unroll
+      for (int q = 0; q < NC; ++q) (side == 0 ? WL0 : WR0)[q] = (side == 0 ? a : dR)[q][0];
+    }
+    done = true;
+  }
+  if (!done) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int cell = f - 1 + side;
+      const int nonlinear = cell_flag(P, flag, cell, 0);
+      const double xi0 = side == 0 ? 0.5 : -0.5;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        const double Wm = fetch(P, st, 0, q, cell - 1, 0, t);
+        const double W0 = fetch(P, st, 0, q, cell, 0, t);
+        const double Wp = fetch(P, st, 0, q, cell + 1, 0, t);
+        const double vm = P.dx * fetch(P, st, 1, q, cell - 1, 0, t);
+        const double vp = P.dx * fetch(P, st, 1, q, cell + 1, 0, t);
+        double c[5], e[5];
+        p1_coeffs(Wm, W0, Wp, vm, vp, c);
+        const Mix mx = shweno_mix(P, Wm, W0, Wp, c, nonlinear);
+        mix_coeffs(mx, Wm, W0, Wp, c, e);
+        taylor_shift(e, xi0, 4);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) (side == 0 ? a : dR)[q][m * 5] = e[m];
+        (side == 0 ? WL0 : WR0)[q] = e[0];
+      }
     }
   }
   // leading term and the linearised problems for the derivatives

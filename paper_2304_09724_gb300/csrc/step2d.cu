@@ -39,8 +39,9 @@ __global__ void __launch_bounds__(TX * TY) coef2d_kernel(Params P, const Ctl* __
                   threadIdx.x, threadIdx.y);
 }
 
-template <int NC, bool FLAGS>
+template <int NC, bool FLAGS, bool CHAR>
 __global__ void __launch_bounds__(SEG) xface2d_kernel(Params P, const Ctl* __restrict__ ctl,
+                                                      const double* s0, const double* s1,
                                                       const double* __restrict__ ycoef,
                                                       const uint8_t* __restrict__ flag,
                                                       double* __restrict__ FX,
@@ -51,18 +52,23 @@ __global__ void __launch_bounds__(SEG) xface2d_kernel(Params P, const Ctl* __res
   const int slice = blockIdx.z;  // 0..2: Gauss point of the rows; 3: corner rows
   const int row = blockIdx.y;    // Gauss: cell row j; corner: corner row jc (y_{jc-1/2})
   if (slice < 3 && row >= P.ny) return;
-  xface_item<NC, FLAGS>(P, step_view(ctl), ycoef, flag, FX, WX, WC, blockIdx.x * SEG, row, slice, smem_raw);
+  const StepView sv = step_view(ctl);
+  xface_item<NC, FLAGS, CHAR>(P, sv, sv.odd ? s1 : s0, ycoef, flag, FX, WX, WC, blockIdx.x * SEG, row, slice,
+                              smem_raw);
 }
 
-template <int NC, bool FLAGS>
+template <int NC, bool FLAGS, bool CHAR>
 __global__ void __launch_bounds__(SEG) yface2d_kernel(Params P, const Ctl* __restrict__ ctl,
+                                                      const double* s0, const double* s1,
                                                       const double* __restrict__ xcoef,
                                                       const uint8_t* __restrict__ flag,
                                                       double* __restrict__ FY,
                                                       double* __restrict__ WY) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (!ctl->active) return;
-  yface_item<NC, FLAGS>(P, step_view(ctl), xcoef, flag, FY, WY, blockIdx.x * SEG, blockIdx.y, blockIdx.z, smem_raw);
+  const StepView sv = step_view(ctl);
+  yface_item<NC, FLAGS, CHAR>(P, sv, sv.odd ? s1 : s0, xcoef, flag, FY, WY, blockIdx.x * SEG, blockIdx.y,
+                              blockIdx.z, smem_raw);
 }
 
 template <int NC>
@@ -103,17 +109,35 @@ Scratch2D carve_scratch2d(const Params& P, double* base) {
   return S;
 }
 
-template <int NC>
+template <int NC, bool CHAR>
 static void init_kernels2d_nc() {
-  cudaFuncSetAttribute(xface2d_kernel<NC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
-  cudaFuncSetAttribute(yface2d_kernel<NC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
-  cudaFuncSetAttribute(xface2d_kernel<NC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
-  cudaFuncSetAttribute(yface2d_kernel<NC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
+  cudaFuncSetAttribute(xface2d_kernel<NC, false, CHAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
+  cudaFuncSetAttribute(yface2d_kernel<NC, false, CHAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
+  cudaFuncSetAttribute(xface2d_kernel<NC, true, CHAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
+  cudaFuncSetAttribute(yface2d_kernel<NC, true, CHAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
 }
 
 void init_kernels2d() {
-  init_kernels2d_nc<1>();
-  init_kernels2d_nc<4>();
+  init_kernels2d_nc<1, false>();
+  init_kernels2d_nc<4, false>();
+  init_kernels2d_nc<4, true>();
+}
+
+// The two face kernels of a step (x-faces with the corner rows, then y-faces).
+template <int NC, bool CHAR>
+static void launch_faces2d(const Params& P, Ctl* ctl, const double* s0, const double* s1,
+                           const uint8_t* flag, const Scratch2D& S, cudaStream_t st, cudaEvent_t* ev) {
+  dim3 xg((P.nx + 1 + SEG - 1) / SEG, P.ny + 1, 4);
+  if (P.flag_mode == FLAG_ALL_NONLINEAR)
+    xface2d_kernel<NC, false, CHAR><<<xg, SEG, kFaceSmem, st>>>(P, ctl, s0, s1, S.ycoef, flag, S.FX, S.WX, S.WC);
+  else
+    xface2d_kernel<NC, true, CHAR><<<xg, SEG, kFaceSmem, st>>>(P, ctl, s0, s1, S.ycoef, flag, S.FX, S.WX, S.WC);
+  if (ev) cudaEventRecord(ev[2], st);
+  dim3 yg((P.ny + 1 + SEG - 1) / SEG, P.nx, 3);
+  if (P.flag_mode == FLAG_ALL_NONLINEAR)
+    yface2d_kernel<NC, false, CHAR><<<yg, SEG, kFaceSmem, st>>>(P, ctl, s0, s1, S.xcoef, flag, S.FY, S.WY);
+  else
+    yface2d_kernel<NC, true, CHAR><<<yg, SEG, kFaceSmem, st>>>(P, ctl, s0, s1, S.xcoef, flag, S.FY, S.WY);
 }
 
 template <int NC>
@@ -124,17 +148,12 @@ static void launch_step2d_nc(const Params& P, Ctl* ctl, const double* s0, const 
   if (ev) cudaEventRecord(ev[0], st);
   coef2d_kernel<NC><<<cg, cb, 0, st>>>(P, ctl, s0, s1, flag, S.ycoef, S.xcoef);
   if (ev) cudaEventRecord(ev[1], st);
-  dim3 xg((P.nx + 1 + SEG - 1) / SEG, P.ny + 1, 4);
-  if (P.flag_mode == FLAG_ALL_NONLINEAR)
-    xface2d_kernel<NC, false><<<xg, SEG, kFaceSmem, st>>>(P, ctl, S.ycoef, flag, S.FX, S.WX, S.WC);
-  else
-    xface2d_kernel<NC, true><<<xg, SEG, kFaceSmem, st>>>(P, ctl, S.ycoef, flag, S.FX, S.WX, S.WC);
-  if (ev) cudaEventRecord(ev[2], st);
-  dim3 yg((P.ny + 1 + SEG - 1) / SEG, P.nx, 3);
-  if (P.flag_mode == FLAG_ALL_NONLINEAR)
-    yface2d_kernel<NC, false><<<yg, SEG, kFaceSmem, st>>>(P, ctl, S.xcoef, flag, S.FY, S.WY);
-  else
-    yface2d_kernel<NC, true><<<yg, SEG, kFaceSmem, st>>>(P, ctl, S.xcoef, flag, S.FY, S.WY);
+  if constexpr (NC == 4) {
+    if (P.charwise) launch_faces2d<NC, true>(P, ctl, s0, s1, flag, S, st, ev);
+    else launch_faces2d<NC, false>(P, ctl, s0, s1, flag, S, st, ev);
+  } else {
+    launch_faces2d<NC, false>(P, ctl, s0, s1, flag, S, st, ev);
+  }
   if (ev) cudaEventRecord(ev[3], st);
   dim3 ug((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
   update2d_kernel<NC><<<ug, cb, 0, st>>>(P, ctl, s0, s1, o0, o1, S.FX, S.WX, S.FY, S.WY, S.WC);

@@ -25,14 +25,16 @@ constexpr size_t kFaceSmem = kEvBytes + sizeof(MixTable);
 
 // Weights of the cells in columns 1..SEG+1 (the cells whose faces the CTA owns).  nl(col)
 // returns whether the cell of column col uses the nonlinear weights.
-template <int NC, typename FlagOf>
+// MIX = false (characteristic-wise reconstruction, whose weights belong to each face point):
+// only the flags are recorded.
+template <int NC, bool MIX, typename FlagOf>
 __device__ __forceinline__ void cell_mixes(const Params& P, const double (*ev)[5][SPAN],
                                            MixTable& mt, FlagOf nl) {
-  for (int it = threadIdx.x; it < NC * (SEG + 1); it += SEG) {
+  for (int it = threadIdx.x; it < (MIX ? NC : 1) * (SEG + 1); it += SEG) {
     const int q = it / (SEG + 1), c = 1 + it % (SEG + 1);
     const int nonlinear = nl(c);
     if (q == 0) mt.lin[c] = !nonlinear;
-    if (!nonlinear) continue;
+    if (!MIX || !nonlinear) continue;
     const double Wm = ev[q][0][c - 1], W0 = ev[q][0][c], Wp = ev[q][0][c + 1];
     double cf[5];
     p1_coeffs(Wm, W0, Wp, ev[NC + q][0][c - 1], ev[NC + q][0][c + 1], cf);
@@ -48,12 +50,10 @@ __device__ __forceinline__ void cell_mixes(const Params& P, const double (*ev)[5
 //   e[p] = A * END[p] . data + (small-stencil terms for p <= 1),
 // with END the constant rows of p1's Taylor coefficients at the end and data = (W-, W0, W+,
 // v-, v+) of order k.
-template <int NC, bool PLUS>
-__device__ __forceinline__ void side_out(const double (*ev)[5][SPAN], int c0, int q, int k, double A,
-                                         double B, double C, bool lin, double e[5]) {
+template <bool PLUS>
+__device__ __forceinline__ void side_out_d(const double d[5], int k, double A, double B, double C,
+                                           bool lin, double e[5]) {
   using namespace shweno_tables;
-  const double d[5] = {ev[q][k][c0], ev[q][k][c0 + 1], ev[q][k][c0 + 2], ev[NC + q][k][c0],
-                       ev[NC + q][k][c0 + 2]};
   if (lin) {  // linear weights: p = p1
 #pragma unroll
     for (int p = 0; p + k <= 4; ++p) e[p] = end_dot<PLUS>(p, d);
@@ -66,30 +66,113 @@ __device__ __forceinline__ void side_out(const double (*ev)[5][SPAN], int c0, in
   else e[0] += (0.5 * B + 1.5 * C) * d[1] + 0.5 * B * d[0] - 0.5 * C * d[2];
   if (k <= 3) e[1] += (B - C) * d[1] - B * d[0] + C * d[2];
 }
+template <int NC, bool PLUS>
+__device__ __forceinline__ void side_out(const double (*ev)[5][SPAN], int c0, int q, int k, double A,
+                                         double B, double C, bool lin, double e[5]) {
+  const double d[5] = {ev[q][k][c0], ev[q][k][c0 + 1], ev[q][k][c0 + 2], ev[NC + q][k][c0],
+                       ev[NC + q][k][c0 + 2]};
+  side_out_d<PLUS>(d, k, A, B, C, lin, e);
+}
+
+// Characteristic-wise counterpart for one face point (Euler, NC = 4): the first-pass data of
+// tangential order k of the four stencil columns c0..c0+3, projected onto the fields of basis
+// Bs; xw[c][f] from {W, Y} (x-face) or {W, V} (y-face), xv[c][f] from the derivative set.
+template <int NC>
+__device__ __forceinline__ void fields_at(const double (*ev)[5][SPAN], const CharBasis<NC>& Bs, int c0,
+                                          int k, double xw[4][NC], double xv[4][NC]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    double w[NC], v[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) { w[q] = ev[q][k][c0 + c]; v[q] = ev[NC + q][k][c0 + c]; }
+    Bs.to_fields(w, xw[c]);
+    Bs.to_fields(v, xv[c]);
+  }
+}
+// Cross-face Taylor coefficients of both sides in physical variables, tangential order k, from
+// the field data: left cell = column 1 (stencil 0..2), right cell = column 2 (stencil 1..3).
+template <int NC>
+__device__ __forceinline__ void char_sides(const CharBasis<NC>& Bs, const double xw[4][NC],
+                                           const double xv[4][NC], int k, const double* AL,
+                                           const double* BL, const double* CL, bool linL,
+                                           const double* AR, const double* BR, const double* CR,
+                                           bool linR, double dl[NC][5], double dr[NC][5]) {
+  double el[NC][5], er[NC][5];
+#pragma unroll
+  for (int f = 0; f < NC; ++f) {
+    const double dL5[5] = {xw[0][f], xw[1][f], xw[2][f], xv[0][f], xv[2][f]};
+    const double dR5[5] = {xw[1][f], xw[2][f], xw[3][f], xv[1][f], xv[3][f]};
+    side_out_d<true>(dL5, k, AL[f], BL[f], CL[f], linL, el[f]);
+    side_out_d<false>(dR5, k, AR[f], BR[f], CR[f], linR, er[f]);
+  }
+#pragma unroll
+  for (int p = 0; p + k <= 4; ++p) {
+    double x[NC], y[NC];
+#pragma unroll
+    for (int f = 0; f < NC; ++f) x[f] = el[f][p];
+    Bs.to_physical(x, y);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) dl[q][p] = y[q];
+#pragma unroll
+    for (int f = 0; f < NC; ++f) x[f] = er[f][p];
+    Bs.to_physical(x, y);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) dr[q][p] = y[q];
+  }
+}
 
 // Face point: both sides' second pass, leading term (Burgers: exact Godunov state; Euler:
 // HLLC), upwinding, CK; returns the time-Taylor coefficients tc[q][0..4].  Left cell in column
 // c0 + 1, right cell in c0 + 2.  dir = 0: x-face (first pass along y), 1: y-face.  NC = 1
-// (Burgers, F = G = u^2/2) or 4 (Euler).
-template <int NC, bool FLAGS>
+// (Burgers, F = G = u^2/2) or 4 (Euler).  CHAR: the second pass runs in the characteristic
+// fields of the Jacobian along the face normal at Wref (the mean of the cell averages next to
+// the point), with its own weights per field and side (the MixTable then holds only the flags).
+template <int NC, bool FLAGS, bool CHAR = false>
 __device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5][SPAN],
-                                           const MixTable& mt, int c0, int dir, double tc[NC][5]) {
+                                           const MixTable& mt, int c0, int dir, double tc[NC][5],
+                                           const double* Wref = nullptr) {
+  static_assert(!CHAR || NC == 4, "characteristic fields are for the Euler system");
   const double g = P.gamma;
   double a[NC][25];
   double dl[NC][5], dr[NC][5];
   double AL[NC], BL[NC], CL[NC], AR[NC], BR[NC], CR[NC];
   // FLAGS = false: every cell uses the nonlinear weights (compile-time, no branch)
   const bool linL = FLAGS && mt.lin[c0 + 1], linR = FLAGS && mt.lin[c0 + 2];
+  CharBasis<NC> Bs;
+  if constexpr (CHAR) {
+    Bs.setup(Wref, g, dir);
+    double xw[4][NC], xv[4][NC];
+    fields_at<NC>(ev, Bs, c0, 0, xw, xv);
 #pragma unroll
-  for (int q = 0; q < NC; ++q) {
-    AL[q] = linL ? 1.0 : mt.A[q][c0 + 1]; BL[q] = linL ? 0.0 : mt.B[q][c0 + 1]; CL[q] = linL ? 0.0 : mt.C[q][c0 + 1];
-    AR[q] = linR ? 1.0 : mt.A[q][c0 + 2]; BR[q] = linR ? 0.0 : mt.B[q][c0 + 2]; CR[q] = linR ? 0.0 : mt.C[q][c0 + 2];
-  }
-  // tangential order 0 first: it carries the leading-term data
+    for (int f = 0; f < NC; ++f) {
+      AL[f] = AR[f] = 1.0;
+      BL[f] = CL[f] = BR[f] = CR[f] = 0.0;
+      if (!linL) {
+        double cf[5];
+        p1_coeffs(xw[0][f], xw[1][f], xw[2][f], xv[0][f], xv[2][f], cf);
+        const Mix m = shweno_mix(P, xw[0][f], xw[1][f], xw[2][f], cf, 1);
+        AL[f] = m.A; BL[f] = m.B; CL[f] = m.C;
+      }
+      if (!linR) {
+        double cf[5];
+        p1_coeffs(xw[1][f], xw[2][f], xw[3][f], xv[1][f], xv[3][f], cf);
+        const Mix m = shweno_mix(P, xw[1][f], xw[2][f], xw[3][f], cf, 1);
+        AR[f] = m.A; BR[f] = m.B; CR[f] = m.C;
+      }
+    }
+    char_sides<NC>(Bs, xw, xv, 0, AL, BL, CL, linL, AR, BR, CR, linR, dl, dr);
+  } else {
 #pragma unroll
-  for (int q = 0; q < NC; ++q) {
-    side_out<NC, true>(ev, c0, q, 0, AL[q], BL[q], CL[q], linL, dl[q]);
-    side_out<NC, false>(ev, c0 + 1, q, 0, AR[q], BR[q], CR[q], linR, dr[q]);
+    for (int q = 0; q < NC; ++q) {
+      AL[q] = linL ? 1.0 : mt.A[q][c0 + 1]; BL[q] = linL ? 0.0 : mt.B[q][c0 + 1]; CL[q] = linL ? 0.0 : mt.C[q][c0 + 1];
+      AR[q] = linR ? 1.0 : mt.A[q][c0 + 2]; BR[q] = linR ? 0.0 : mt.B[q][c0 + 2]; CR[q] = linR ? 0.0 : mt.C[q][c0 + 2];
+    }
+    // tangential order 0 first: it carries the leading-term data
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      side_out<NC, true>(ev, c0, q, 0, AL[q], BL[q], CL[q], linL, dl[q]);
+      side_out<NC, false>(ev, c0 + 1, q, 0, AR[q], BR[q], CR[q], linR, dr[q]);
+    }
   }
   double WL[NC], WR[NC], Ws[NC];
 #pragma unroll
@@ -101,10 +184,16 @@ __device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     if (k > 0) {
+      if constexpr (CHAR) {
+        double xw[4][NC], xv[4][NC];
+        fields_at<NC>(ev, Bs, c0, k, xw, xv);
+        char_sides<NC>(Bs, xw, xv, k, AL, BL, CL, linL, AR, BR, CR, linR, dl, dr);
+      } else {
 #pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        side_out<NC, true>(ev, c0, q, k, AL[q], BL[q], CL[q], linL, dl[q]);
-        side_out<NC, false>(ev, c0 + 1, q, k, AR[q], BR[q], CR[q], linR, dr[q]);
+        for (int q = 0; q < NC; ++q) {
+          side_out<NC, true>(ev, c0, q, k, AL[q], BL[q], CL[q], linL, dl[q]);
+          side_out<NC, false>(ev, c0 + 1, q, k, AR[q], BR[q], CR[q], linR, dr[q]);
+        }
       }
     }
 #pragma unroll
@@ -227,8 +316,8 @@ __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv,
 
 // x-face Gauss points (slice 0..2, cell row `row`) or corner points (slice 3, corner row `row`
 // at y_{row-1/2}) of faces x_{f0-1/2} .. x_{f0+SEG-3/2}; SEG threads, smem_raw of kFaceSmem bytes.
-template <int NC, bool FLAGS>
-__device__ __forceinline__ void xface_item(const Params& P, const StepView& sv,
+template <int NC, bool FLAGS, bool CHAR = false>
+__device__ __forceinline__ void xface_item(const Params& P, const StepView& sv, const double* st,
                                            const double* __restrict__ ycoef,
                                            const uint8_t* __restrict__ flag, double* __restrict__ FX,
                                            double* __restrict__ WX, double* __restrict__ WC, int f0,
@@ -263,7 +352,7 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv,
   }
   __syncthreads();
   // cell column c holds cell i = f0 + c - 2; a corner row uses the rows below and above
-  cell_mixes<NC>(P, ev, mt, [&](int c) {
+  cell_mixes<NC, !CHAR>(P, ev, mt, [&](int c) {
     const int i = f0 + c - 2;
     return slice < 3 ? cell_flag(P, flag, i, row)
                      : (cell_flag(P, flag, i, row - 1) | cell_flag(P, flag, i, row));
@@ -272,7 +361,18 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv,
   const int fi = f0 + threadIdx.x;  // face x_{fi-1/2}
   if (fi > P.nx) return;  // no barrier follows
   double tc[NC][5];
-  face_point<NC, FLAGS>(P, ev, mt, threadIdx.x, 0, tc);
+  double Wref[NC];
+  if constexpr (CHAR) {  // cells next to the face point (the four around a corner)
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      if (slice < 3)
+        Wref[q] = 0.5 * (fetch(P, st, 0, q, fi - 1, row, sv.t) + fetch(P, st, 0, q, fi, row, sv.t));
+      else
+        Wref[q] = 0.25 * (fetch(P, st, 0, q, fi - 1, row - 1, sv.t) + fetch(P, st, 0, q, fi, row - 1, sv.t) +
+                          fetch(P, st, 0, q, fi - 1, row, sv.t) + fetch(P, st, 0, q, fi, row, sv.t));
+    }
+  }
+  face_point<NC, FLAGS, CHAR>(P, ev, mt, threadIdx.x, 0, tc, Wref);
   const double dt = sv.dt;
   if (slice < 3) {
     double Fh[NC], We[NC];
@@ -290,8 +390,8 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv,
 }
 
 // y-face Gauss points (slice 0..2) of column `col`, faces y_{f0-1/2} .. y_{f0+SEG-3/2}.
-template <int NC, bool FLAGS>
-__device__ __forceinline__ void yface_item(const Params& P, const StepView& sv,
+template <int NC, bool FLAGS, bool CHAR = false>
+__device__ __forceinline__ void yface_item(const Params& P, const StepView& sv, const double* st,
                                            const double* __restrict__ xcoef,
                                            const uint8_t* __restrict__ flag, double* __restrict__ FY,
                                            double* __restrict__ WY, int f0, int col, int slice,
@@ -314,12 +414,18 @@ __device__ __forceinline__ void yface_item(const Params& P, const StepView& sv,
     for (int k = 0; k < 5; ++k) ev[rq][k][r] = e[k];
   }
   __syncthreads();
-  cell_mixes<NC>(P, ev, mt, [&](int c) { return cell_flag(P, flag, col, f0 + c - 2); });
+  cell_mixes<NC, !CHAR>(P, ev, mt, [&](int c) { return cell_flag(P, flag, col, f0 + c - 2); });
   __syncthreads();
   const int fj = f0 + threadIdx.x;  // face y_{fj-1/2}
   if (fj > P.ny) return;
   double tc[NC][5];
-  face_point<NC, FLAGS>(P, ev, mt, threadIdx.x, 1, tc);
+  double Wref[NC];
+  if constexpr (CHAR) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+      Wref[q] = 0.5 * (fetch(P, st, 0, q, col, fj - 1, sv.t) + fetch(P, st, 0, q, col, fj, sv.t));
+  }
+  face_point<NC, FLAGS, CHAR>(P, ev, mt, threadIdx.x, 1, tc, Wref);
   double Gh[NC], We[NC];
   lobatto<NC>(tc, sv.dt, P.gamma, 1, Gh, We);
 #pragma unroll

@@ -2,6 +2,7 @@
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2304_09724_gb300 import workloads as WL
 from tests import gpu_util as U
 
@@ -78,3 +79,26 @@ def test_per_cell_flags():
     flag = (rng.random(64) < 0.5).astype(np.uint8)
     g, o = U.steps_both(wl, [0.002] * 3, flag=flag, flag_mode=2)
     U.check(g, o, U.fields(wl), shocked=False, what="per-cell flags, smooth", wl=wl)
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-10])
+def test_epsilon_option(eps):
+    """The epsilon of the nonlinear weights is an option (shweno_opts.eps): parity with the
+    oracle's same epsilon on a shocked and a smooth 1D run, and on a 2D Riemann problem."""
+    for wl, T, shocked in ((WL.lax(200), 0.5, True), (WL.euler1d_sine(40), 0.5, False)):
+        sol = U.solver_of(wl, eps=eps)
+        sol.set_state(wl.state)
+        t, n = sol.run(T, wl.cfl)
+        g = sol.get_state()
+        sol.close()
+        o, n_o, t_o = O.run(U.problem_of(wl, eps=eps), wl.state, T, wl.cfl)
+        assert n == n_o
+        U.check(g, o, U.fields(wl), shocked=shocked, what=f"{wl.name} eps={eps}", wl=wl)
+    wl = WL.riemann2d(24, WL.LAX_LIU_SHOCKS)
+    sol = U.solver_of(wl, eps=eps)
+    sol.set_state(wl.state)
+    sol.run(0.03, wl.cfl)
+    g = sol.get_state()
+    sol.close()
+    o, _, _ = O.run(U.problem_of(wl, eps=eps), wl.state, 0.03, wl.cfl)
+    U.check(g, o, U.fields(wl), shocked=True, what=f"2D eps={eps}", wl=wl)
