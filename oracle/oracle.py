@@ -34,6 +34,7 @@ class Problem(ctypes.Structure):
         ("eps", ctypes.c_double),
         ("gam", ctypes.c_double * 3),
         ("charwise", ctypes.c_int32),
+        ("quintic", ctypes.c_int32),
     ]
 
 
@@ -62,6 +63,11 @@ def lib():
         L.orc_smoothness.restype = ctypes.c_double
         L.orc_weights.argtypes = [dp, dp, ctypes.c_int, ctypes.c_double, dp, dp]
         L.orc_recon.argtypes = [dp, dp, ctypes.c_int, ctypes.c_double, dp, ctypes.c_double, dp]
+        L.orc_recon_deg.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp,
+                                    ctypes.c_double, dp]
+        L.orc_big_poly_deg.argtypes = [dp, dp, ctypes.c_int, dp]
+        L.orc_smoothness_deg.argtypes = [dp]
+        L.orc_smoothness_deg.restype = ctypes.c_double
         L.orc_quadrature.argtypes = [dp, dp, dp, dp]
         L.orc_burgers_godunov.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_burgers_godunov.restype = ctypes.c_double
@@ -95,7 +101,8 @@ def _f64(a):
 
 
 def make_problem(dim, eq, nx, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, bc=(0, 0, 0, 0),
-                 inflow=None, linear=False, eps=1e-6, gam=GAMMA_LINEAR, charwise=False) -> Problem:
+                 inflow=None, linear=False, eps=1e-6, gam=GAMMA_LINEAR, charwise=False,
+                 quintic=False) -> Problem:
     P = Problem()
     P.dim, P.eq, P.nx, P.ny = dim, eq, nx, (ny if dim == 2 else 1)
     P.x0, P.y0 = x0, y0
@@ -113,6 +120,7 @@ def make_problem(dim, eq, nx, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=1.4, b
     for k in range(3):
         P.gam[k] = gam[k]
     P.charwise = 1 if charwise else 0
+    P.quintic = 1 if quintic else 0
     return P
 
 
@@ -141,6 +149,25 @@ def recon(Wb, v, xi, linear=False, eps=1e-6, gam=GAMMA_LINEAR):
     """d^k p/dxi^k (k = 0..4) of the SHWENO polynomial of the middle cell at xi."""
     d = np.zeros(5)
     lib().orc_recon(_dp(_f64(Wb)), _dp(_f64(v)), int(linear), eps, _dp(_f64(gam)), xi, _dp(d))
+    return d
+
+
+def big_poly_deg(Wb, v3, quintic):
+    """p1 coefficients c[0..5] from v3 = (h V_-1, h V_0, h V_+1) (reading R1 ignores h V_0)."""
+    c = np.zeros(6)
+    lib().orc_big_poly_deg(_dp(_f64(Wb)), _dp(_f64(v3)), int(quintic), _dp(c))
+    return c
+
+
+def smoothness_deg(c6):
+    return lib().orc_smoothness_deg(_dp(_f64(c6)))
+
+
+def recon_deg(Wb, v3, xi, quintic, linear=False, eps=1e-6, gam=GAMMA_LINEAR):
+    """recon() with v3 = (h V_-1, h V_0, h V_+1) and the choice of reading R1 / R1'."""
+    d = np.zeros(5)
+    lib().orc_recon_deg(_dp(_f64(Wb)), _dp(_f64(v3)), int(quintic), int(linear), eps, _dp(_f64(gam)),
+                        xi, _dp(d))
     return d
 
 

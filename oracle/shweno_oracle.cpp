@@ -52,6 +52,7 @@ struct Problem {
   double eps;            // epsilon in the nonlinear weights
   double gam[3];         // linear weights gamma_1..3 (Section 2.4)
   int32_t charwise;      // 1: Euler reconstructions across a face in characteristic fields
+  int32_t quintic;       // 1: reading R1' (quintic p1 that also matches the cell's own V)
 };
 
 int ncomp(const Problem& P) {
@@ -117,74 +118,80 @@ void invert(int n, const double* A, double* Ainv) {
 // ----------------------------------------------------------------------------------------
 // Step 1: the SHWENO reconstruction in one dimension (Section 2.4), on the local coordinate
 // xi = (x - x_j)/h in [-1/2, 1/2].  Input for cell j: the cell averages Wb = (W_{j-1}, W_j,
-// W_{j+1}) and the derivative averages scaled by h, v = (h V_{j-1}, h V_{j+1}).  Polynomials are
-// held as monomial coefficients c[0..4] in xi.
+// W_{j+1}) and the derivative averages scaled by h, v = (h V_{j-1}, h V_j, h V_{j+1}) (the
+// middle one is used by reading R1' only).  Polynomials are held as monomial coefficients
+// c[0..5] in xi (c[5] = 0 for the quartic of reading R1).
 // ----------------------------------------------------------------------------------------
 double mono_avg(int k, double a, double b) {  // (1/(b-a)) * integral_a^b xi^k d xi, b - a = 1
   return (std::pow(b, k + 1) - std::pow(a, k + 1)) / (k + 1);
 }
 
-// Quartic p1 on the big stencil: its averages over cells -1, 0, +1 equal Wb, and the averages
-// of its xi-derivative over cells -1 and +1 equal v (the reading of the omitted procedure).
-// The five conditions are written out as rows of a 5x5 matrix; its inverse is formed once by
-// Gaussian elimination and applied to (Wb, v).
-const double* big_poly_inverse() {
-  static double Minv[25];
-  static bool ready = false;
-  if (!ready) {
-    double A[25];
+// p1 on the big stencil: its averages over cells -1, 0, +1 equal Wb, and the averages of its
+// xi-derivative over cells -1 and +1 equal v- and v+ (reading R1 of the omitted procedure: a
+// quartic, five conditions); reading R1' adds the derivative average over cell 0 (v0) and
+// raises the degree to five.  The conditions are written out as rows of a matrix; its inverse
+// is formed once by Gaussian elimination and applied to the data.
+const double* big_poly_inverse(int quintic) {
+  static double Minv[2][36];
+  static bool ready[2] = {false, false};
+  const int n = quintic ? 6 : 5;
+  if (!ready[quintic]) {
+    double A[36];
     for (int l = -1; l <= 1; ++l)
-      for (int k = 0; k < 5; ++k) A[(l + 1) * 5 + k] = mono_avg(k, l - 0.5, l + 0.5);
-    const int outer[2] = {-1, 1};
-    for (int r = 0; r < 2; ++r) {
-      int l = outer[r];
+      for (int k = 0; k < n; ++k) A[(l + 1) * n + k] = mono_avg(k, l - 0.5, l + 0.5);
+    const int quint_cells[3] = {-1, 1, 0}, quart_cells[2] = {-1, 1};
+    const int* dcell = quintic ? quint_cells : quart_cells;
+    for (int r = 0; r < n - 3; ++r) {
+      int l = dcell[r];
       // average of p' over cell l = p(l + 1/2) - p(l - 1/2)
-      for (int k = 0; k < 5; ++k) A[(3 + r) * 5 + k] = std::pow(l + 0.5, k) - std::pow(l - 0.5, k);
+      for (int k = 0; k < n; ++k) A[(3 + r) * n + k] = std::pow(l + 0.5, k) - std::pow(l - 0.5, k);
     }
-    invert(5, A, Minv);
-    ready = true;
+    invert(n, A, Minv[quintic]);
+    ready[quintic] = true;
   }
-  return Minv;
+  return Minv[quintic];
 }
-void big_poly(const double Wb[3], const double v[2], double c[5]) {
-  const double* Minv = big_poly_inverse();
-  const double rhs[5] = {Wb[0], Wb[1], Wb[2], v[0], v[1]};
-  for (int k = 0; k < 5; ++k) {
+void big_poly(const double Wb[3], const double v[3], int quintic, double c[6]) {
+  const double* Minv = big_poly_inverse(quintic);
+  const int n = quintic ? 6 : 5;
+  const double rhs[6] = {Wb[0], Wb[1], Wb[2], v[0], v[2], v[1]};
+  for (int k = 0; k < n; ++k) {
     double s = 0.0;
-    for (int r = 0; r < 5; ++r) s += Minv[k * 5 + r] * rhs[r];
+    for (int r = 0; r < n; ++r) s += Minv[k * n + r] * rhs[r];
     c[k] = s;
   }
+  if (!quintic) c[5] = 0.0;
 }
 // Linear polynomials on the two small stencils, matching two cell averages each.
-void small_polys(const double Wb[3], double c2[5], double c3[5]) {
-  for (int k = 0; k < 5; ++k) c2[k] = c3[k] = 0.0;
+void small_polys(const double Wb[3], double c2[6], double c3[6]) {
+  for (int k = 0; k < 6; ++k) c2[k] = c3[k] = 0.0;
   c2[0] = Wb[1]; c2[1] = Wb[1] - Wb[0];   // {I_{j-1}, I_j}
   c3[0] = Wb[1]; c3[1] = Wb[2] - Wb[1];   // {I_j, I_{j+1}}
 }
 // Jiang-Shu smoothness indicator beta = sum_{a>=1} integral_{-1/2}^{1/2} (d^a p / d xi^a)^2,
 // computed exactly by squaring the derivative polynomial and integrating its monomials.
-double smoothness(const double c[5]) {
+double smoothness(const double c[6]) {
   double beta = 0.0;
-  double d[5];
-  for (int k = 0; k < 5; ++k) d[k] = c[k];
-  for (int a = 1; a <= 4; ++a) {
-    double nd[5] = {0};
-    for (int k = 1; k < 5; ++k) nd[k - 1] = k * d[k];
-    for (int k = 0; k < 5; ++k) d[k] = nd[k];
-    double sq[9] = {0};
-    for (int i = 0; i < 5; ++i)
-      for (int j = 0; j < 5; ++j) sq[i + j] += d[i] * d[j];
-    for (int k = 0; k < 9; k += 2) beta += sq[k] * 2.0 * std::ldexp(1.0, -(k + 1)) / (k + 1);
+  double d[6];
+  for (int k = 0; k < 6; ++k) d[k] = c[k];
+  for (int a = 1; a <= 5; ++a) {
+    double nd[6] = {0};
+    for (int k = 1; k < 6; ++k) nd[k - 1] = k * d[k];
+    for (int k = 0; k < 6; ++k) d[k] = nd[k];
+    double sq[11] = {0};
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) sq[i + j] += d[i] * d[j];
+    for (int k = 0; k < 11; k += 2) beta += sq[k] * 2.0 * std::ldexp(1.0, -(k + 1)) / (k + 1);
   }
   return beta;
 }
 // Nonlinear weights of the simple-WENO form: tau = ((|b1-b2| + |b1-b3|)/2)^2 and
 // w_l proportional to gamma_l (1 + tau/(beta_l + eps)).  linear=1 returns gamma itself.
-void shweno_weights(const double Wb[3], const double v[2], int linear, double eps,
+void shweno_weights(const double Wb[3], const double v[3], int quintic, int linear, double eps,
                     const double gam[3], double w[3]) {
   if (linear) { for (int l = 0; l < 3; ++l) w[l] = gam[l]; return; }
-  double c1[5], c2[5], c3[5];
-  big_poly(Wb, v, c1);
+  double c1[6], c2[6], c3[6];
+  big_poly(Wb, v, quintic, c1);
   small_polys(Wb, c2, c3);
   double b[3] = {smoothness(c1), smoothness(c2), smoothness(c3)};
   double tau = 0.5 * (std::fabs(b[0] - b[1]) + std::fabs(b[0] - b[2]));
@@ -196,20 +203,20 @@ void shweno_weights(const double Wb[3], const double v[2], int linear, double ep
 // Combined SHWENO polynomial p = w1 (p1/g1 - g2/g1 p2 - g3/g1 p3) + w2 p2 + w3 p3 for given
 // weights.  With w = gamma it is p1.  The same weights serve the value and every derivative
 // (end of Section 2.1.2).
-void shweno_poly(const double Wb[3], const double v[2], const double w[3], const double gam[3],
-                 double c[5]) {
-  double c1[5], c2[5], c3[5];
-  big_poly(Wb, v, c1);
+void shweno_poly(const double Wb[3], const double v[3], int quintic, const double w[3],
+                 const double gam[3], double c[6]) {
+  double c1[6], c2[6], c3[6];
+  big_poly(Wb, v, quintic, c1);
   small_polys(Wb, c2, c3);
-  for (int k = 0; k < 5; ++k)
+  for (int k = 0; k < 6; ++k)
     c[k] = w[0] * (c1[k] / gam[0] - gam[1] / gam[0] * c2[k] - gam[2] / gam[0] * c3[k]) +
            w[1] * c2[k] + w[2] * c3[k];
 }
 // d^k p / d xi^k at xi, k = 0..4.
-void poly_derivs(const double c[5], double xi, double d[5]) {
+void poly_derivs(const double c[6], double xi, double d[5]) {
   for (int k = 0; k < 5; ++k) {
     double s = 0.0, xp = 1.0;
-    for (int i = k; i < 5; ++i) {
+    for (int i = k; i < 6; ++i) {
       double f = 1.0;
       for (int q = 0; q < k; ++q) f *= (i - q);
       s += c[i] * f * xp;
@@ -627,11 +634,11 @@ int cell_flag(const State& S, int i, int j) {
 }
 
 // One 1D SHWENO reconstruction evaluated at xi: derivatives d^k/dxi^k, k = 0..4.
-void recon_eval(const Problem& P, const double Wb[3], const double v[2], int nonlinear,
+void recon_eval(const Problem& P, const double Wb[3], const double v[3], int nonlinear,
                 double xi, double d[5]) {
-  double w[3], c[5];
-  shweno_weights(Wb, v, P.linear || !nonlinear, P.eps, P.gam, w);
-  shweno_poly(Wb, v, w, P.gam, c);
+  double w[3], c[6];
+  shweno_weights(Wb, v, P.quintic, P.linear || !nonlinear, P.eps, P.gam, w);
+  shweno_poly(Wb, v, P.quintic, w, P.gam, c);
   poly_derivs(c, xi, d);
 }
 
@@ -684,21 +691,18 @@ void step1d(const Problem& P, const State& S, double dt, double* Wn, double* Vn)
     face_basis(P, 0, S, fc - 1, 0, fc, 0, Rm, Lm);
     for (int side = 0; side < 2; ++side) {
       const int cell = fc - 1 + side;
-      double Wc[3][4], Vc[2][4];  // stencil data in the reconstruction fields
+      double Wc[3][4], Vc[3][4];  // stencil data in the reconstruction fields
       for (int r = 0; r < 3; ++r) {
         double w[4];
         for (int q = 0; q < nc; ++q) w[q] = fetch(S, 0, q, cell - 1 + r, 0);
         project(nc, Lm, w, Wc[r]);
-      }
-      for (int r = 0; r < 2; ++r) {
-        double w[4];
-        for (int q = 0; q < nc; ++q) w[q] = h * fetch(S, 1, q, cell - 1 + 2 * r, 0);
+        for (int q = 0; q < nc; ++q) w[q] = h * fetch(S, 1, q, cell - 1 + r, 0);
         project(nc, Lm, w, Vc[r]);
       }
       double dk[4][5];
       for (int k = 0; k < nc; ++k) {
         double Wb[3] = {Wc[0][k], Wc[1][k], Wc[2][k]};
-        double v[2] = {Vc[0][k], Vc[1][k]};
+        double v[3] = {Vc[0][k], Vc[1][k], Vc[2][k]};
         recon_eval(P, Wb, v, cell_flag(S, cell, 0), side == 0 ? 0.5 : -0.5, dk[k]);
       }
       for (int m = 0; m <= ORD; ++m) {
@@ -733,7 +737,8 @@ void ypass(const State& S, int i, int j, double eta, double out[2][4][5]) {
     for (int q = 0; q < nc; ++q) {
       int fa = set == 0 ? 0 : 1, fd = set == 0 ? 2 : 3;
       double Wb[3] = {fetch(S, fa, q, i, j - 1), fetch(S, fa, q, i, j), fetch(S, fa, q, i, j + 1)};
-      double v[2] = {P.dy * fetch(S, fd, q, i, j - 1), P.dy * fetch(S, fd, q, i, j + 1)};
+      double v[3] = {P.dy * fetch(S, fd, q, i, j - 1), P.dy * fetch(S, fd, q, i, j),
+                     P.dy * fetch(S, fd, q, i, j + 1)};
       double d[5];
       recon_eval(P, Wb, v, cell_flag(S, i, j), eta, d);
       for (int n = 0; n <= ORD; ++n) out[set][q][n] = d[n] / std::pow(P.dy, n);
@@ -748,7 +753,8 @@ void xpass(const State& S, int i, int j, double xi, double out[2][4][5]) {
     for (int q = 0; q < nc; ++q) {
       int fa = set == 0 ? 0 : 2, fd = set == 0 ? 1 : 3;
       double Wb[3] = {fetch(S, fa, q, i - 1, j), fetch(S, fa, q, i, j), fetch(S, fa, q, i + 1, j)};
-      double v[2] = {P.dx * fetch(S, fd, q, i - 1, j), P.dx * fetch(S, fd, q, i + 1, j)};
+      double v[3] = {P.dx * fetch(S, fd, q, i - 1, j), P.dx * fetch(S, fd, q, i, j),
+                     P.dx * fetch(S, fd, q, i + 1, j)};
       double d[5];
       recon_eval(P, Wb, v, cell_flag(S, i, j), xi, d);
       for (int m = 0; m <= ORD; ++m) out[set][q][m] = d[m] / std::pow(P.dx, m);
@@ -785,14 +791,14 @@ void second_pass(const Problem& P, int dir, double hn, const double line_in[4][2
       double w[3];
       {
         double Wb[3] = {line[base][0][q][0], line[base + 1][0][q][0], line[base + 2][0][q][0]};
-        double v[2] = {hn * line[base][1][q][0], hn * line[base + 2][1][q][0]};
-        shweno_weights(Wb, v, P.linear || !fl, P.eps, P.gam, w);
+        double v[3] = {hn * line[base][1][q][0], hn * line[base + 1][1][q][0], hn * line[base + 2][1][q][0]};
+        shweno_weights(Wb, v, P.quintic, P.linear || !fl, P.eps, P.gam, w);
       }
       for (int k = 0; k <= ORD; ++k) {
         double Wb[3] = {line[base][0][q][k], line[base + 1][0][q][k], line[base + 2][0][q][k]};
-        double v[2] = {hn * line[base][1][q][k], hn * line[base + 2][1][q][k]};
-        double c[5], d[5];
-        shweno_poly(Wb, v, w, P.gam, c);
+        double v[3] = {hn * line[base][1][q][k], hn * line[base + 1][1][q][k], hn * line[base + 2][1][q][k]};
+        double c[6], d[5];
+        shweno_poly(Wb, v, P.quintic, w, P.gam, c);
         poly_derivs(c, xi, d);
         for (int p = 0; p + k <= ORD; ++p) (side == 0 ? dL : dR)[q][p][k] = d[p] / std::pow(hn, p);
       }
@@ -1040,15 +1046,40 @@ extern "C" {
 typedef Problem orc_problem;
 
 // Section 2.4 reading: p1 coefficients, smoothness indicators, weights, combined polynomial.
-void orc_big_poly(const double* Wb, const double* v, double* c) { big_poly(Wb, v, c); }
-double orc_smoothness(const double* c) { return smoothness(c); }
+// v = (h V_{-1}, h V_{+1}) for the quartic (reading R1); the *_deg forms take
+// v = (h V_{-1}, h V_0, h V_{+1}) and quintic = 1 for reading R1'.  Coefficients c[0..5].
+void orc_big_poly(const double* Wb, const double* v, double* c) {
+  const double v3[3] = {v[0], 0.0, v[1]};
+  double c6[6];
+  big_poly(Wb, v3, 0, c6);
+  for (int k = 0; k < 5; ++k) c[k] = c6[k];
+}
+void orc_big_poly_deg(const double* Wb, const double* v, int quintic, double* c) {
+  big_poly(Wb, v, quintic, c);
+}
+double orc_smoothness(const double* c) {
+  const double c6[6] = {c[0], c[1], c[2], c[3], c[4], 0.0};
+  return smoothness(c6);
+}
+double orc_smoothness_deg(const double* c) { return smoothness(c); }
 void orc_weights(const double* Wb, const double* v, int linear, double eps, const double* gam,
-                 double* w) { shweno_weights(Wb, v, linear, eps, gam, w); }
+                 double* w) {
+  const double v3[3] = {v[0], 0.0, v[1]};
+  shweno_weights(Wb, v3, 0, linear, eps, gam, w);
+}
 void orc_recon(const double* Wb, const double* v, int linear, double eps, const double* gam,
                double xi, double* d) {
-  double w[3], c[5];
-  shweno_weights(Wb, v, linear, eps, gam, w);
-  shweno_poly(Wb, v, w, gam, c);
+  const double v3[3] = {v[0], 0.0, v[1]};
+  double w[3], c[6];
+  shweno_weights(Wb, v3, 0, linear, eps, gam, w);
+  shweno_poly(Wb, v3, 0, w, gam, c);
+  poly_derivs(c, xi, d);
+}
+void orc_recon_deg(const double* Wb, const double* v, int quintic, int linear, double eps,
+                   const double* gam, double xi, double* d) {
+  double w[3], c[6];
+  shweno_weights(Wb, v, quintic, linear, eps, gam, w);
+  shweno_poly(Wb, v, quintic, w, gam, c);
   poly_derivs(c, xi, d);
 }
 void orc_quadrature(double* lob_nodes, double* lob_w, double* gauss_nodes, double* gauss_w) {
@@ -1141,9 +1172,10 @@ void orc_weight_deviation2d(const orc_problem* P, const double* W, const double*
             double h = pass == 0 ? P->dy : P->dx;
             double Wb[3] = {fetch(S, fa, q, i - di, j - dj), fetch(S, fa, q, i, j),
                             fetch(S, fa, q, i + di, j + dj)};
-            double v[2] = {h * fetch(S, fd, q, i - di, j - dj), h * fetch(S, fd, q, i + di, j + dj)};
+            double v[3] = {h * fetch(S, fd, q, i - di, j - dj), h * fetch(S, fd, q, i, j),
+                           h * fetch(S, fd, q, i + di, j + dj)};
             double w[3];
-            shweno_weights(Wb, v, 0, P->eps, P->gam, w);
+            shweno_weights(Wb, v, P->quintic, 0, P->eps, P->gam, w);
             for (int l = 0; l < 3; ++l) dev = std::fmax(dev, std::fabs(w[l] - P->gam[l]) / P->gam[l]);
           }
       out[(size_t)j * P->nx + i] = dev;
