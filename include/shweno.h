@@ -93,6 +93,10 @@ typedef struct {
                          two cell averages; 2D: the two order-0 values of the pass along the
                          face at that point), projected with the left eigenvectors and mapped
                          back with the right ones; no effect for Burgers */
+  int32_t quintic;    /* not in the paper's text, which omits the procedure.  0: reading R1, the
+                         quartic p1 matching the three cell averages and the outer derivative
+                         averages; 1: reading R1', a quintic p1 that also matches the cell's own
+                         derivative average (Section 2.4) */
 } shweno_opts;
 
 typedef struct shweno_handle shweno_handle;
@@ -226,9 +230,9 @@ shweno_status shweno_get_flags(shweno_handle* h, uint8_t* out, int on_device);
 typedef struct shweno_batch shweno_batch;
 
 /* Groups n handles.  cuda_stream: stream of the batch's work (NULL: its own).
- * Errors: INVALID (null or bad handle; a 2D handle created with charwise = 1, whose
- * characteristic face items the persistent kernel does not carry), STATE (a per-cell-flag
- * handle without flags or flag network). */
+ * Errors: INVALID (null or bad handle; a 2D handle created with charwise = 1 or any handle
+ * created with quintic = 1, whose items the persistent kernel does not carry), STATE (a
+ * per-cell-flag handle without flags or flag network). */
 shweno_status shweno_batch_create(shweno_handle* const* hs, int n, void* cuda_stream,
                                   shweno_batch** out);
 

@@ -289,9 +289,10 @@ shweno_status shweno_create(const shweno_grid* grid, double gamma, const shweno_
   for (int a = 0; a < dim; ++a)
     if ((bc->kind[2 * a] == SHWENO_BC_PERIODIC) != (bc->kind[2 * a + 1] == SHWENO_BC_PERIODIC))
       return fail(nullptr, SHWENO_E_INVALID, "periodic boundaries must be paired");
-  shweno_opts o{0, 1e-6, {0.994, 0.003, 0.003}, 0};
+  shweno_opts o{0, 1e-6, {0.994, 0.003, 0.003}, 0, 0};
   if (opts) o = *opts;
-  if (o.flag_mode < 0 || o.flag_mode > 2 || o.charwise < 0 || o.charwise > 1 || !(o.eps > 0.0) ||
+  if (o.flag_mode < 0 || o.flag_mode > 2 || o.charwise < 0 || o.charwise > 1 || o.quintic < 0 ||
+      o.quintic > 1 || !(o.eps > 0.0) ||
       !(o.gam[0] > 0 && o.gam[1] > 0 && o.gam[2] > 0) ||
       std::fabs(o.gam[0] + o.gam[1] + o.gam[2] - 1.0) > 1e-12)
     return fail(nullptr, SHWENO_E_INVALID, "invalid options");
@@ -317,6 +318,7 @@ shweno_status shweno_create(const shweno_grid* grid, double gamma, const shweno_
   for (int k = 0; k < 3; ++k) P.gam[k] = o.gam[k];
   P.flag_mode = o.flag_mode;
   P.charwise = grid->eq == SHWENO_EULER ? o.charwise : 0;
+  P.quintic = o.quintic;
   shweno::finalize_params(P);
 
   h->cells = (size_t)P.nx * P.ny;

@@ -114,8 +114,8 @@ __device__ void do_item(const BatchProblem& B, int kind, long long idx, unsigned
       double* out = sv.odd ? B.s0 : B.s1;
       for (int k = threadIdx.x; k <= nc; k += BT) {
         double Fh[3], We[3];
-        if (P.ncomp == 1) face1d_point<1>(P, st, B.flag, c0 + k, sv.t, sv.dt, Fh, We);
-        else face1d_point<3>(P, st, B.flag, c0 + k, sv.t, sv.dt, Fh, We);
+        if (P.ncomp == 1) face1d_point<1, false>(P, st, B.flag, c0 + k, sv.t, sv.dt, Fh, We);
+        else face1d_point<3, false>(P, st, B.flag, c0 + k, sv.t, sv.dt, Fh, We);
         for (int q = 0; q < P.ncomp; ++q) { FH[q * (B.tile1d + 1) + k] = Fh[q]; WE[q * (B.tile1d + 1) + k] = We[q]; }
       }
       __syncthreads();
@@ -434,8 +434,11 @@ shweno_status shweno_batch_create(shweno_handle* const* hs, int n, void* cuda_st
   size_t cap_need = 0;
   for (int p = 0; p < n; ++p) {
     if (!hs[p] || !handle_view(hs[p], &b->views[p])) { delete b; return SHWENO_E_INVALID; }
-    // the persistent kernel carries the componentwise 2D face items only
-    if (b->views[p].P.dim == 2 && b->views[p].P.charwise) { delete b; return SHWENO_E_INVALID; }
+    // the persistent kernel carries reading R1 and the componentwise 2D face items only
+    if ((b->views[p].P.dim == 2 && b->views[p].P.charwise) || b->views[p].P.quintic) {
+      delete b;
+      return SHWENO_E_INVALID;
+    }
     if (b->views[p].P.flag_mode == FLAG_PER_CELL && !b->views[p].flags && !b->views[p].learned) {
       delete b;
       return SHWENO_E_STATE;

@@ -7,6 +7,10 @@ In the local coordinate xi in [-1/2, 1/2] the data of cell j are W- = W_{j-1}, W
 W+ = W_{j+1}, v- = h V_{j-1}, v+ = h V_{j+1}.  With the symmetric combinations
   s = W- + W+, dv = v+ - v-   (even part of p1)   and   a = W+ - W-, sv = v- + v+   (odd part)
 the monomial coefficients of p1 split into c0, c2, c4 (from W0, s, dv) and c1, c3 (from a, sv).
+
+Reading R1' (option): a quintic p1 that also matches v0 = h V_j.  Its even part is R1's (the
+odd monomials do not enter W0, s or dv); its odd part c1, c3, c5 comes from (a, sv, v0).  The
+Q-prefixed constants below are that variant.
 """
 import os
 
@@ -46,6 +50,36 @@ def derive():
         for j in range(i, 5):
             bq[(i, j)] = beta.coeff(cc[i], 1).coeff(cc[j], 1) if i != j else beta.coeff(cc[i], 2)
     return coef, bq, (W0, s, dv, a, sv), ends, (Wm, W0, Wp, vm, vp)
+
+
+def derive_quintic():
+    c = sp.symbols("c0:6")
+    Wm, W0, Wp, vm, v0, vp = sp.symbols("Wm W0 Wp vm v0 vp")
+    P = sum(c[k] * xi ** k for k in range(6))
+    eqs = [sp.integrate(P, (xi, l - half, l + half)) - w for l, w in ((-1, Wm), (0, W0), (1, Wp))]
+    eqs += [P.subs(xi, l + half) - P.subs(xi, l - half) - w for l, w in ((-1, vm), (0, v0), (1, vp))]
+    sol = sp.solve(eqs, c)
+    s, dv, a, sv = sp.symbols("s dv a sv")
+    sub = {Wm: (s - a) / 2, Wp: (s + a) / 2, vm: (sv - dv) / 2, vp: (sv + dv) / 2}
+    coef = {}
+    for k in range(6):
+        e = sp.expand(sol[c[k]].subs(sub))
+        coef[k] = {v: e.coeff(v) for v in (W0, s, dv, a, sv, v0)}
+    P1 = P.subs(sol)
+    ends = {}
+    data = (Wm, W0, Wp, vm, v0, vp)
+    for tag, x0 in (("P", half), ("M", -half)):
+        for m in range(5):
+            e = sp.expand(sp.diff(P1, xi, m).subs(xi, x0) / sp.factorial(m))
+            ends[(tag, m)] = {v: e.coeff(v) for v in data}
+    cc = sp.symbols("k0:6")
+    Pc = sum(cc[k] * xi ** k for k in range(6))
+    beta = sp.expand(sum(sp.integrate(sp.diff(Pc, xi, d) ** 2, (xi, -half, half)) for d in range(1, 6)))
+    bq = {}
+    for i in range(1, 6):
+        for j in range(i, 6):
+            bq[(i, j)] = beta.coeff(cc[i], 1).coeff(cc[j], 1) if i != j else beta.coeff(cc[i], 2)
+    return coef, bq, (W0, s, dv, a, sv, v0), ends, data
 
 
 def frac(r):
@@ -88,6 +122,34 @@ def main():
     lines.append("// smoothness indicator of p1: beta1 = sum_{i<=j} B_ij c_i c_j (i, j >= 1)")
     for (i, j), val in bq.items():
         lines.append(f"constexpr double BETA_{i}{j} = {frac(val)};")
+    qcoef, qbq, qnames, qends, qdata = derive_quintic()
+    for k in range(6):
+        for v in qnames:
+            if k % 2 == 0 and k < 5:  # even part: R1's constants
+                assert qcoef[k][v] == coef[k].get(v, 0), (k, v)
+    lines.append("// Reading R1' (quintic p1, data (W-, W0, W+, v-, v0, v+)): odd monomial coefficients")
+    lines.append("// c_k = QP1_C<k>_a a + QP1_C<k>_sv sv + QP1_C<k>_v0 v0 (k = 1, 3, 5); even ones as R1.")
+    for k in (1, 3, 5):
+        for v in qnames[3:]:
+            lines.append(f"constexpr double QP1_C{k}_{v} = {frac(qcoef[k][v])};")
+    lines.append("// R1' Taylor coefficients at the ends over (W-, W0, W+, v-, v0, v+)")
+    for tag in ("P", "M"):
+        for m in range(5):
+            for iv, v in enumerate(qdata):
+                lines.append(f"constexpr double QEND_{tag}_{m}_{iv} = {frac(qends[(tag, m)][v])};")
+    lines.append("template <bool PLUS>")
+    lines.append("__host__ __device__ __forceinline__ double qend_dot(int p, const double d[6]) {")
+    lines.append("  switch (p) {")
+    for m in range(5):
+        tp = " + ".join(f"QEND_P_{m}_{iv} * d[{iv}]" for iv in range(6))
+        tm = " + ".join(f"QEND_M_{m}_{iv} * d[{iv}]" for iv in range(6))
+        lines.append(f"    case {m}: return PLUS ? ({tp}) : ({tm});")
+    lines.append("  }")
+    lines.append("  return 0.0;")
+    lines.append("}")
+    lines.append("// R1' smoothness indicator: beta1 = sum_{i<=j} QB_ij c_i c_j (i, j >= 1)")
+    for (i, j), val in qbq.items():
+        lines.append(f"constexpr double QBETA_{i}{j} = {frac(val)};")
     lines.append("// 3-point Gauss nodes on [-1/2, 1/2] (offset) and weights")
     lines.append("constexpr double GAUSS_G = 0.38729833462074168852;  // sqrt(15)/10")
     lines.append("constexpr double GAUSS_W0 = (5.0 / 18.0), GAUSS_W1 = (8.0 / 18.0);")

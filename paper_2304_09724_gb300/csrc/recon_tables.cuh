@@ -103,6 +103,105 @@ constexpr double BETA_24 = (21.0 / 5.0);
 constexpr double BETA_33 = (3129.0 / 80.0);
 constexpr double BETA_34 = 0.0;
 constexpr double BETA_44 = (87617.0 / 140.0);
+// Reading R1' (quintic p1, data (W-, W0, W+, v-, v0, v+)): odd monomial coefficients
+// c_k = QP1_C<k>_a a + QP1_C<k>_sv sv + QP1_C<k>_v0 v0 (k = 1, 3, 5); even ones as R1.
+constexpr double QP1_C1_a = (-27.0 / 64.0);
+constexpr double QP1_C1_sv = (19.0 / 192.0);
+constexpr double QP1_C1_v0 = (79.0 / 48.0);
+constexpr double QP1_C3_a = (15.0 / 8.0);
+constexpr double QP1_C3_sv = (-11.0 / 24.0);
+constexpr double QP1_C3_v0 = (-17.0 / 6.0);
+constexpr double QP1_C5_a = (-3.0 / 4.0);
+constexpr double QP1_C5_sv = (1.0 / 4.0);
+constexpr double QP1_C5_v0 = 1.0;
+// R1' Taylor coefficients at the ends over (W-, W0, W+, v-, v0, v+)
+constexpr double QEND_P_0_0 = (11.0 / 60.0);
+constexpr double QEND_P_0_1 = (19.0 / 30.0);
+constexpr double QEND_P_0_2 = (11.0 / 60.0);
+constexpr double QEND_P_0_3 = (1.0 / 20.0);
+constexpr double QEND_P_0_4 = (1.0 / 2.0);
+constexpr double QEND_P_0_5 = (-1.0 / 20.0);
+constexpr double QEND_P_1_0 = (1.0 / 4.0);
+constexpr double QEND_P_1_1 = -2.0;
+constexpr double QEND_P_1_2 = (7.0 / 4.0);
+constexpr double QEND_P_1_3 = (1.0 / 12.0);
+constexpr double QEND_P_1_4 = (-1.0 / 6.0);
+constexpr double QEND_P_1_5 = (-5.0 / 12.0);
+constexpr double QEND_P_2_0 = (-11.0 / 8.0);
+constexpr double QEND_P_2_1 = -1.0;
+constexpr double QEND_P_2_2 = (19.0 / 8.0);
+constexpr double QEND_P_2_3 = (-3.0 / 8.0);
+constexpr double QEND_P_2_4 = -3.0;
+constexpr double QEND_P_2_5 = (-3.0 / 8.0);
+constexpr double QEND_P_3_0 = -1.0;
+constexpr double QEND_P_3_1 = 2.0;
+constexpr double QEND_P_3_2 = -1.0;
+constexpr double QEND_P_3_3 = (-1.0 / 3.0);
+constexpr double QEND_P_3_4 = (-1.0 / 3.0);
+constexpr double QEND_P_3_5 = (2.0 / 3.0);
+constexpr double QEND_P_4_0 = (11.0 / 8.0);
+constexpr double QEND_P_4_1 = 1.0;
+constexpr double QEND_P_4_2 = (-19.0 / 8.0);
+constexpr double QEND_P_4_3 = (3.0 / 8.0);
+constexpr double QEND_P_4_4 = (5.0 / 2.0);
+constexpr double QEND_P_4_5 = (7.0 / 8.0);
+constexpr double QEND_M_0_0 = (11.0 / 60.0);
+constexpr double QEND_M_0_1 = (19.0 / 30.0);
+constexpr double QEND_M_0_2 = (11.0 / 60.0);
+constexpr double QEND_M_0_3 = (1.0 / 20.0);
+constexpr double QEND_M_0_4 = (-1.0 / 2.0);
+constexpr double QEND_M_0_5 = (-1.0 / 20.0);
+constexpr double QEND_M_1_0 = (-7.0 / 4.0);
+constexpr double QEND_M_1_1 = 2.0;
+constexpr double QEND_M_1_2 = (-1.0 / 4.0);
+constexpr double QEND_M_1_3 = (-5.0 / 12.0);
+constexpr double QEND_M_1_4 = (-1.0 / 6.0);
+constexpr double QEND_M_1_5 = (1.0 / 12.0);
+constexpr double QEND_M_2_0 = (19.0 / 8.0);
+constexpr double QEND_M_2_1 = -1.0;
+constexpr double QEND_M_2_2 = (-11.0 / 8.0);
+constexpr double QEND_M_2_3 = (3.0 / 8.0);
+constexpr double QEND_M_2_4 = 3.0;
+constexpr double QEND_M_2_5 = (3.0 / 8.0);
+constexpr double QEND_M_3_0 = 1.0;
+constexpr double QEND_M_3_1 = -2.0;
+constexpr double QEND_M_3_2 = 1.0;
+constexpr double QEND_M_3_3 = (2.0 / 3.0);
+constexpr double QEND_M_3_4 = (-1.0 / 3.0);
+constexpr double QEND_M_3_5 = (-1.0 / 3.0);
+constexpr double QEND_M_4_0 = (-19.0 / 8.0);
+constexpr double QEND_M_4_1 = 1.0;
+constexpr double QEND_M_4_2 = (11.0 / 8.0);
+constexpr double QEND_M_4_3 = (-7.0 / 8.0);
+constexpr double QEND_M_4_4 = (-5.0 / 2.0);
+constexpr double QEND_M_4_5 = (-3.0 / 8.0);
+template <bool PLUS>
+__host__ __device__ __forceinline__ double qend_dot(int p, const double d[6]) {
+  switch (p) {
+    case 0: return PLUS ? (QEND_P_0_0 * d[0] + QEND_P_0_1 * d[1] + QEND_P_0_2 * d[2] + QEND_P_0_3 * d[3] + QEND_P_0_4 * d[4] + QEND_P_0_5 * d[5]) : (QEND_M_0_0 * d[0] + QEND_M_0_1 * d[1] + QEND_M_0_2 * d[2] + QEND_M_0_3 * d[3] + QEND_M_0_4 * d[4] + QEND_M_0_5 * d[5]);
+    case 1: return PLUS ? (QEND_P_1_0 * d[0] + QEND_P_1_1 * d[1] + QEND_P_1_2 * d[2] + QEND_P_1_3 * d[3] + QEND_P_1_4 * d[4] + QEND_P_1_5 * d[5]) : (QEND_M_1_0 * d[0] + QEND_M_1_1 * d[1] + QEND_M_1_2 * d[2] + QEND_M_1_3 * d[3] + QEND_M_1_4 * d[4] + QEND_M_1_5 * d[5]);
+    case 2: return PLUS ? (QEND_P_2_0 * d[0] + QEND_P_2_1 * d[1] + QEND_P_2_2 * d[2] + QEND_P_2_3 * d[3] + QEND_P_2_4 * d[4] + QEND_P_2_5 * d[5]) : (QEND_M_2_0 * d[0] + QEND_M_2_1 * d[1] + QEND_M_2_2 * d[2] + QEND_M_2_3 * d[3] + QEND_M_2_4 * d[4] + QEND_M_2_5 * d[5]);
+    case 3: return PLUS ? (QEND_P_3_0 * d[0] + QEND_P_3_1 * d[1] + QEND_P_3_2 * d[2] + QEND_P_3_3 * d[3] + QEND_P_3_4 * d[4] + QEND_P_3_5 * d[5]) : (QEND_M_3_0 * d[0] + QEND_M_3_1 * d[1] + QEND_M_3_2 * d[2] + QEND_M_3_3 * d[3] + QEND_M_3_4 * d[4] + QEND_M_3_5 * d[5]);
+    case 4: return PLUS ? (QEND_P_4_0 * d[0] + QEND_P_4_1 * d[1] + QEND_P_4_2 * d[2] + QEND_P_4_3 * d[3] + QEND_P_4_4 * d[4] + QEND_P_4_5 * d[5]) : (QEND_M_4_0 * d[0] + QEND_M_4_1 * d[1] + QEND_M_4_2 * d[2] + QEND_M_4_3 * d[3] + QEND_M_4_4 * d[4] + QEND_M_4_5 * d[5]);
+  }
+  return 0.0;
+}
+// R1' smoothness indicator: beta1 = sum_{i<=j} QB_ij c_i c_j (i, j >= 1)
+constexpr double QBETA_11 = 1.0;
+constexpr double QBETA_12 = 0.0;
+constexpr double QBETA_13 = (1.0 / 2.0);
+constexpr double QBETA_14 = 0.0;
+constexpr double QBETA_15 = (1.0 / 8.0);
+constexpr double QBETA_22 = (13.0 / 3.0);
+constexpr double QBETA_23 = 0.0;
+constexpr double QBETA_24 = (21.0 / 5.0);
+constexpr double QBETA_25 = 0.0;
+constexpr double QBETA_33 = (3129.0 / 80.0);
+constexpr double QBETA_34 = 0.0;
+constexpr double QBETA_35 = (14127.0 / 224.0);
+constexpr double QBETA_44 = (87617.0 / 140.0);
+constexpr double QBETA_45 = 0.0;
+constexpr double QBETA_55 = (252337135.0 / 16128.0);
 // 3-point Gauss nodes on [-1/2, 1/2] (offset) and weights
 constexpr double GAUSS_G = 0.38729833462074168852;  // sqrt(15)/10
 constexpr double GAUSS_W0 = (5.0 / 18.0), GAUSS_W1 = (8.0 / 18.0);

@@ -28,6 +28,7 @@ struct Params {
   double gam[3];          // linear weights
   int32_t flag_mode;      // FLAG_*
   int32_t charwise;       // 1: Euler reconstructions across a face in characteristic fields
+  int32_t quintic;        // 1: reading R1' (quintic p1 that also matches the cell's own V)
   // Cauchy-Kovalevskaya scale factors (m+1)/((k+1) dx) and (n+1)/((k+1) dy), set by the host
   double ckx[5][4], cky[5][4];
   double igam[3];  // 1 / gam, set by the host
@@ -227,6 +228,61 @@ __device__ __forceinline__ void mix_coeffs(const Mix& m, double Wm, double W0, d
   C[2] = m.A * c[2];
   C[3] = m.A * c[3];
   C[4] = m.A * c[4];
+}
+
+// ---- reading R1' (option): quintic p1 that also matches v0 = h * the cell's own derivative
+// average.  Its even coefficients are R1's; the odd ones c1, c3, c5 come from (a, sv, v0).
+// The templates below take Q = false for R1 (c[5] = 0 and v0 unused) and Q = true for R1'.
+template <bool Q>
+__device__ __forceinline__ void p1_coeffs_t(double Wm, double W0, double Wp, double vm, double v0,
+                                            double vp, double c[6]) {
+  using namespace shweno_tables;
+  if constexpr (!Q) {
+    p1_coeffs(Wm, W0, Wp, vm, vp, c);
+    c[5] = 0.0;
+  } else {
+    const double s = Wm + Wp, dv = vp - vm, a = Wp - Wm, sv = vm + vp;
+    c[0] = P1_C0_W0 * W0 + P1_C0_s * s + P1_C0_dv * dv;
+    c[1] = QP1_C1_a * a + QP1_C1_sv * sv + QP1_C1_v0 * v0;
+    c[2] = P1_C2_W0 * W0 + P1_C2_s * s + P1_C2_dv * dv;
+    c[3] = QP1_C3_a * a + QP1_C3_sv * sv + QP1_C3_v0 * v0;
+    c[4] = P1_C4_W0 * W0 + P1_C4_s * s + P1_C4_dv * dv;
+    c[5] = QP1_C5_a * a + QP1_C5_sv * sv + QP1_C5_v0 * v0;
+  }
+}
+
+template <bool Q>
+__device__ __forceinline__ Mix shweno_mix_t(const Params& P, double Wm, double W0, double Wp,
+                                            const double c[6], int nonlinear) {
+  using namespace shweno_tables;
+  if constexpr (!Q) {
+    return shweno_mix(P, Wm, W0, Wp, c, nonlinear);
+  } else {
+    if (!nonlinear) return Mix{1.0, 0.0, 0.0};
+    const double b1 = c[1] * (QBETA_11 * c[1] + QBETA_13 * c[3] + QBETA_15 * c[5]) +
+                      c[3] * (QBETA_33 * c[3] + QBETA_35 * c[5]) + QBETA_55 * c[5] * c[5] +
+                      c[2] * (QBETA_22 * c[2] + QBETA_24 * c[4]) + QBETA_44 * c[4] * c[4];
+    const double d2 = W0 - Wm, d3 = Wp - W0;
+    const double b2 = d2 * d2, b3 = d3 * d3;
+    double tau = 0.5 * (fabs(b1 - b2) + fabs(b1 - b3));
+    tau = tau * tau;
+    const double e1 = b1 + P.eps, e2 = b2 + P.eps, e3 = b3 + P.eps;
+    const double e12 = e1 * e2, r = 1.0 / (e12 * e3);
+    const double w1 = P.gam[0] * (1.0 + tau * (e2 * e3 * r));
+    const double w2 = P.gam[1] * (1.0 + tau * (e1 * e3 * r));
+    const double w3 = P.gam[2] * (1.0 + tau * (e12 * r));
+    const double inv = 1.0 / (w1 + w2 + w3);
+    const double A = w1 * inv * P.igam[0];
+    return Mix{A, w2 * inv - A * P.gam[1], w3 * inv - A * P.gam[2]};
+  }
+}
+
+// Combined-polynomial coefficients C[0..K-1], K = 5 (R1) or 6 (R1').
+template <bool Q>
+__device__ __forceinline__ void mix_coeffs_t(const Mix& m, double Wm, double W0, double Wp,
+                                             const double c[6], double C[6]) {
+  mix_coeffs(m, Wm, W0, Wp, c, C);
+  if constexpr (Q) C[5] = m.A * c[5];
 }
 
 // ------------------------------------------------------------------ physics
@@ -463,6 +519,16 @@ struct CharBasis {
     }
   }
 };
+
+// Normalised Taylor coefficients about xi0 of a polynomial of degree D given by its monomial
+// coefficients e[0..D] (in place; repeated synthetic division).
+template <int D>
+__device__ __forceinline__ void taylor_shift_d(double* e, double xi0) {
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int k = D - 1; k >= i; --k) e[k] += xi0 * e[k + 1];
+}
 
 // Normalised Taylor coefficients e[m] of the polynomial sum C[k] xi^k about xi0, m <= mmax
 // (repeated synthetic division).

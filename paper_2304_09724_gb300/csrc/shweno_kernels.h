@@ -10,8 +10,8 @@ namespace shweno {
 
 // Scratch buffers of one 2D step (all device memory owned by the handle).
 struct Scratch2D {
-  double* ycoef;  // [2 sets][ncomp][5 coefs][ny+2][nx+4]
-  double* xcoef;  // [2 sets][ncomp][5 coefs][nx][ny+4]
+  double* ycoef;  // [2 sets][ncomp][KC coefs][ny+2][nx+4], KC = 5 (R1) or 6 (R1')
+  double* xcoef;  // [2 sets][ncomp][KC coefs][nx][ny+4]
   double* FX;     // [3 gauss][ncomp][ny][nx+1]  time-averaged x-flux per Gauss point
   double* WX;     // [3 gauss][ncomp][ny][nx+1]  state at t_{n+1} per Gauss point
   double* FY;     // [3 gauss][ncomp][ny+1][nx]
@@ -30,6 +30,10 @@ void launch_step2d(const Params& P, Ctl* ctl, const double* s0, const double* s1
                    cudaEvent_t* ev);
 size_t scratch2d_doubles(const Params& P);
 void init_kernels2d();  // kernel attributes (dynamic shared memory); call before any capture
+void init_kernels2d_quintic();
+void launch_step2d_quintic(const Params& P, Ctl* ctl, const double* s0, const double* s1,
+                           double* o0, double* o1, const uint8_t* flag, const Scratch2D& S,
+                           cudaStream_t st, cudaEvent_t* ev);
 Scratch2D carve_scratch2d(const Params& P, double* base);
 void launch_features2d(const Params& P, const Ctl* ctl, const double* s0, const double* s1,
                        float* out, cudaStream_t st);

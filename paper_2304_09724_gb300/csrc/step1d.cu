@@ -3,7 +3,8 @@
 //             (Section 2.4 reading), leading term (exact Burgers / HLLC, Eq. 2.5), linearised
 //             derivative Riemann problems (Eq. 2.8), Cauchy-Kovalevskaya (Eq. 2.6), Lobatto
 //             time quadrature of the flux (Eq. 2.9, Remark 2) and the state at t_{n+1}
-//             (Eq. 2.12, Remark 1).  Writes F-hat and W(t_{n+1}) per face.
+//             (Eq. 2.12, Remark 1).  Writes F-hat and W(t_{n+1}) per face.  Instantiated for
+//             reading R1 (quartic p1) and the R1' option (quintic p1).
 //   update1d: one thread per cell: Eq. (2.2) for the averages, Eq. (2.11) for the derivative
 //             averages; fused max characteristic rate of the new state (next CFL step) and the
 //             physical-state check.
@@ -14,7 +15,7 @@
 
 namespace shweno {
 
-template <int NC>
+template <int NC, bool Q>
 __global__ void __launch_bounds__(128) face1d_kernel(Params P, const Ctl* __restrict__ ctl,
                                                      const double* s0, const double* s1,
                                                      const uint8_t* __restrict__ flag,
@@ -25,7 +26,7 @@ __global__ void __launch_bounds__(128) face1d_kernel(Params P, const Ctl* __rest
   if (f > P.nx) return;
   const StepView sv = step_view(ctl);
   double Fh[NC], We[NC];
-  face1d_point<NC>(P, sv.odd ? s1 : s0, flag, f, sv.t, sv.dt, Fh, We);
+  face1d_point<NC, Q>(P, sv.odd ? s1 : s0, flag, f, sv.t, sv.dt, Fh, We);
 #pragma unroll
   for (int q = 0; q < NC; ++q) {
     FH[(size_t)q * (P.nx + 1) + f] = Fh[q];
@@ -67,10 +68,14 @@ void launch_step1d(const Params& P, Ctl* ctl, const double* s0, const double* s1
   const int nf = P.nx + 1;
   const int b = 128;
   if (ev) cudaEventRecord(ev[0], st);
-  if (P.ncomp == 1)
-    face1d_kernel<1><<<(nf + b - 1) / b, b, 0, st>>>(P, ctl, s0, s1, flag, FH, WE);
-  else
-    face1d_kernel<3><<<(nf + b - 1) / b, b, 0, st>>>(P, ctl, s0, s1, flag, FH, WE);
+  const dim3 g((nf + b - 1) / b);
+  if (P.ncomp == 1) {
+    if (P.quintic) face1d_kernel<1, true><<<g, b, 0, st>>>(P, ctl, s0, s1, flag, FH, WE);
+    else face1d_kernel<1, false><<<g, b, 0, st>>>(P, ctl, s0, s1, flag, FH, WE);
+  } else {
+    if (P.quintic) face1d_kernel<3, true><<<g, b, 0, st>>>(P, ctl, s0, s1, flag, FH, WE);
+    else face1d_kernel<3, false><<<g, b, 0, st>>>(P, ctl, s0, s1, flag, FH, WE);
+  }
   if (ev) cudaEventRecord(ev[1], st);
   update1d_kernel<<<(P.nx + 255) / 256, 256, 0, st>>>(P, ctl, s0, s1, o0, o1, FH, WE);
   if (ev) cudaEventRecord(ev[2], st);

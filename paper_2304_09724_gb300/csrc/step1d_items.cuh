@@ -8,8 +8,8 @@ namespace shweno {
 
 // One interface x_{f-1/2} (between cells f-1 and f) of state st: SHWENO reconstruction of both
 // neighbours, leading term, linearised derivative problems, CK, Lobatto flux; returns the
-// time-averaged flux Fh and the state We at t + dt.
-template <int NC>
+// time-averaged flux Fh and the state We at t + dt.  Q: reading R1' (quintic p1).
+template <int NC, bool Q = false>
 __device__ __forceinline__ void face1d_point(const Params& P, const double* st,
                                              const uint8_t* __restrict__ flag, int f, double t,
                                              double dt, double Fh[NC], double We[NC]) {
@@ -29,7 +29,8 @@ __device__ __forceinline__ void face1d_point(const Params& P, const double* st,
       const int cell = f - 1 + side;
       const int nonlinear = cell_flag(P, flag, cell, 0);
       const double xi0 = side == 0 ? 0.5 : -0.5;
-      double d[5][NC], x[5][NC];  // stencil data W-, W0, W+, h V-, h V+: physical, then fields
+      constexpr int ND = Q ? 6 : 5;
+      double d[ND][NC], x[ND][NC];  // W-, W0, W+, h V-, h V+ (, h V0): physical, then fields
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
         d[0][q] = fetch(P, st, 0, q, cell - 1, 0, t);
@@ -37,17 +38,18 @@ __device__ __forceinline__ void face1d_point(const Params& P, const double* st,
         d[2][q] = fetch(P, st, 0, q, cell + 1, 0, t);
         d[3][q] = P.dx * fetch(P, st, 1, q, cell - 1, 0, t);
         d[4][q] = P.dx * fetch(P, st, 1, q, cell + 1, 0, t);
+        if constexpr (Q) d[5][q] = P.dx * fetch(P, st, 1, q, cell, 0, t);
       }
 #pragma unroll
-      for (int r = 0; r < 5; ++r) B.to_fields(d[r], x[r]);
-      double e[NC][5];
+      for (int r = 0; r < ND; ++r) B.to_fields(d[r], x[r]);
+      double e[NC][6];
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
-        double c[5];
-        p1_coeffs(x[0][k], x[1][k], x[2][k], x[3][k], x[4][k], c);
-        const Mix mx = shweno_mix(P, x[0][k], x[1][k], x[2][k], c, nonlinear);
-        mix_coeffs(mx, x[0][k], x[1][k], x[2][k], c, e[k]);
-        taylor_shift(e[k], xi0, 4);
+        double c[6];
+        p1_coeffs_t<Q>(x[0][k], x[1][k], x[2][k], x[3][k], Q ? x[ND - 1][k] : 0.0, x[4][k], c);
+        const Mix mx = shweno_mix_t<Q>(P, x[0][k], x[1][k], x[2][k], c, nonlinear);
+        mix_coeffs_t<Q>(mx, x[0][k], x[1][k], x[2][k], c, e[k]);
+        taylor_shift_d<Q ? 5 : 4>(e[k], xi0);
       }
 #pragma unroll
       for (int m = 0; m < 5; ++m) {
@@ -76,11 +78,12 @@ __device__ __forceinline__ void face1d_point(const Params& P, const double* st,
         const double Wp = fetch(P, st, 0, q, cell + 1, 0, t);
         const double vm = P.dx * fetch(P, st, 1, q, cell - 1, 0, t);
         const double vp = P.dx * fetch(P, st, 1, q, cell + 1, 0, t);
-        double c[5], e[5];
-        p1_coeffs(Wm, W0, Wp, vm, vp, c);
-        const Mix mx = shweno_mix(P, Wm, W0, Wp, c, nonlinear);
-        mix_coeffs(mx, Wm, W0, Wp, c, e);
-        taylor_shift(e, xi0, 4);
+        const double v0 = Q ? P.dx * fetch(P, st, 1, q, cell, 0, t) : 0.0;
+        double c[6], e[6];
+        p1_coeffs_t<Q>(Wm, W0, Wp, vm, v0, vp, c);
+        const Mix mx = shweno_mix_t<Q>(P, Wm, W0, Wp, c, nonlinear);
+        mix_coeffs_t<Q>(mx, Wm, W0, Wp, c, e);
+        taylor_shift_d<Q ? 5 : 4>(e, xi0);
 #pragma unroll
         for (int m = 0; m < 5; ++m) (side == 0 ? a : dR)[q][m * 5] = e[m];
         (side == 0 ? WL0 : WR0)[q] = e[0];

@@ -27,7 +27,7 @@ constexpr size_t kFaceSmem = kEvBytes + sizeof(MixTable);
 // returns whether the cell of column col uses the nonlinear weights.
 // MIX = false (characteristic-wise reconstruction, whose weights belong to each face point):
 // only the flags are recorded.
-template <int NC, bool MIX, typename FlagOf>
+template <int NC, bool MIX, bool Q, typename FlagOf>
 __device__ __forceinline__ void cell_mixes(const Params& P, const double (*ev)[5][SPAN],
                                            MixTable& mt, FlagOf nl) {
   for (int it = threadIdx.x; it < (MIX ? NC : 1) * (SEG + 1); it += SEG) {
@@ -36,9 +36,9 @@ __device__ __forceinline__ void cell_mixes(const Params& P, const double (*ev)[5
     if (q == 0) mt.lin[c] = !nonlinear;
     if (!MIX || !nonlinear) continue;
     const double Wm = ev[q][0][c - 1], W0 = ev[q][0][c], Wp = ev[q][0][c + 1];
-    double cf[5];
-    p1_coeffs(Wm, W0, Wp, ev[NC + q][0][c - 1], ev[NC + q][0][c + 1], cf);
-    const Mix m = shweno_mix(P, Wm, W0, Wp, cf, 1);
+    double cf[6];
+    p1_coeffs_t<Q>(Wm, W0, Wp, ev[NC + q][0][c - 1], ev[NC + q][0][c], ev[NC + q][0][c + 1], cf);
+    const Mix m = shweno_mix_t<Q>(P, Wm, W0, Wp, cf, 1);
     mt.A[q][c] = m.A;
     mt.B[q][c] = m.B;
     mt.C[q][c] = m.C;
@@ -50,28 +50,35 @@ __device__ __forceinline__ void cell_mixes(const Params& P, const double (*ev)[5
 //   e[p] = A * END[p] . data + (small-stencil terms for p <= 1),
 // with END the constant rows of p1's Taylor coefficients at the end and data = (W-, W0, W+,
 // v-, v+) of order k.
-template <bool PLUS>
-__device__ __forceinline__ void side_out_d(const double d[5], int k, double A, double B, double C,
+// d = (W-, W0, W+, v-, v+) for reading R1, (W-, W0, W+, v-, v0, v+) for R1' (Q).
+template <bool PLUS, bool Q = false>
+__device__ __forceinline__ void side_out_d(const double* d, int k, double A, double B, double C,
                                            bool lin, double e[5]) {
   using namespace shweno_tables;
   if (lin) {  // linear weights: p = p1
 #pragma unroll
-    for (int p = 0; p + k <= 4; ++p) e[p] = end_dot<PLUS>(p, d);
+    for (int p = 0; p + k <= 4; ++p) e[p] = Q ? qend_dot<PLUS>(p, d) : end_dot<PLUS>(p, d);
     return;
   }
 #pragma unroll
-  for (int p = 0; p + k <= 4; ++p) e[p] = A * end_dot<PLUS>(p, d);
+  for (int p = 0; p + k <= 4; ++p) e[p] = A * (Q ? qend_dot<PLUS>(p, d) : end_dot<PLUS>(p, d));
   // p2 = W0 + (W0 - W-) xi and p3 = W0 + (W+ - W0) xi: value and slope at the end
   if (PLUS) e[0] += (1.5 * B + 0.5 * C) * d[1] - 0.5 * B * d[0] + 0.5 * C * d[2];
   else e[0] += (0.5 * B + 1.5 * C) * d[1] + 0.5 * B * d[0] - 0.5 * C * d[2];
   if (k <= 3) e[1] += (B - C) * d[1] - B * d[0] + C * d[2];
 }
-template <int NC, bool PLUS>
+template <int NC, bool PLUS, bool Q = false>
 __device__ __forceinline__ void side_out(const double (*ev)[5][SPAN], int c0, int q, int k, double A,
                                          double B, double C, bool lin, double e[5]) {
-  const double d[5] = {ev[q][k][c0], ev[q][k][c0 + 1], ev[q][k][c0 + 2], ev[NC + q][k][c0],
-                       ev[NC + q][k][c0 + 2]};
-  side_out_d<PLUS>(d, k, A, B, C, lin, e);
+  if constexpr (Q) {
+    const double d[6] = {ev[q][k][c0], ev[q][k][c0 + 1], ev[q][k][c0 + 2], ev[NC + q][k][c0],
+                         ev[NC + q][k][c0 + 1], ev[NC + q][k][c0 + 2]};
+    side_out_d<PLUS, true>(d, k, A, B, C, lin, e);
+  } else {
+    const double d[5] = {ev[q][k][c0], ev[q][k][c0 + 1], ev[q][k][c0 + 2], ev[NC + q][k][c0],
+                         ev[NC + q][k][c0 + 2]};
+    side_out_d<PLUS>(d, k, A, B, C, lin, e);
+  }
 }
 
 // Characteristic-wise counterpart for one face point (Euler, NC = 4): the first-pass data of
@@ -91,7 +98,7 @@ __device__ __forceinline__ void fields_at(const double (*ev)[5][SPAN], const Cha
 }
 // Cross-face Taylor coefficients of both sides in physical variables, tangential order k, from
 // the field data: left cell = column 1 (stencil 0..2), right cell = column 2 (stencil 1..3).
-template <int NC>
+template <int NC, bool Q>
 __device__ __forceinline__ void char_sides(const CharBasis<NC>& Bs, const double xw[4][NC],
                                            const double xv[4][NC], int k, const double* AL,
                                            const double* BL, const double* CL, bool linL,
@@ -100,10 +107,17 @@ __device__ __forceinline__ void char_sides(const CharBasis<NC>& Bs, const double
   double el[NC][5], er[NC][5];
 #pragma unroll
   for (int f = 0; f < NC; ++f) {
-    const double dL5[5] = {xw[0][f], xw[1][f], xw[2][f], xv[0][f], xv[2][f]};
-    const double dR5[5] = {xw[1][f], xw[2][f], xw[3][f], xv[1][f], xv[3][f]};
-    side_out_d<true>(dL5, k, AL[f], BL[f], CL[f], linL, el[f]);
-    side_out_d<false>(dR5, k, AR[f], BR[f], CR[f], linR, er[f]);
+    if constexpr (Q) {
+      const double dL[6] = {xw[0][f], xw[1][f], xw[2][f], xv[0][f], xv[1][f], xv[2][f]};
+      const double dR[6] = {xw[1][f], xw[2][f], xw[3][f], xv[1][f], xv[2][f], xv[3][f]};
+      side_out_d<true, true>(dL, k, AL[f], BL[f], CL[f], linL, el[f]);
+      side_out_d<false, true>(dR, k, AR[f], BR[f], CR[f], linR, er[f]);
+    } else {
+      const double dL5[5] = {xw[0][f], xw[1][f], xw[2][f], xv[0][f], xv[2][f]};
+      const double dR5[5] = {xw[1][f], xw[2][f], xw[3][f], xv[1][f], xv[3][f]};
+      side_out_d<true>(dL5, k, AL[f], BL[f], CL[f], linL, el[f]);
+      side_out_d<false>(dR5, k, AR[f], BR[f], CR[f], linR, er[f]);
+    }
   }
 #pragma unroll
   for (int p = 0; p + k <= 4; ++p) {
@@ -127,7 +141,7 @@ __device__ __forceinline__ void char_sides(const CharBasis<NC>& Bs, const double
 // (Burgers, F = G = u^2/2) or 4 (Euler).  CHAR: the second pass runs in the characteristic
 // fields of the Jacobian along the face normal at Wref (the mean of the cell averages next to
 // the point), with its own weights per field and side (the MixTable then holds only the flags).
-template <int NC, bool FLAGS, bool CHAR = false>
+template <int NC, bool FLAGS, bool CHAR = false, bool Q = false>
 __device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5][SPAN],
                                            const MixTable& mt, int c0, int dir, double tc[NC][5],
                                            const double* Wref = nullptr) {
@@ -148,19 +162,19 @@ __device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5
       AL[f] = AR[f] = 1.0;
       BL[f] = CL[f] = BR[f] = CR[f] = 0.0;
       if (!linL) {
-        double cf[5];
-        p1_coeffs(xw[0][f], xw[1][f], xw[2][f], xv[0][f], xv[2][f], cf);
-        const Mix m = shweno_mix(P, xw[0][f], xw[1][f], xw[2][f], cf, 1);
+        double cf[6];
+        p1_coeffs_t<Q>(xw[0][f], xw[1][f], xw[2][f], xv[0][f], xv[1][f], xv[2][f], cf);
+        const Mix m = shweno_mix_t<Q>(P, xw[0][f], xw[1][f], xw[2][f], cf, 1);
         AL[f] = m.A; BL[f] = m.B; CL[f] = m.C;
       }
       if (!linR) {
-        double cf[5];
-        p1_coeffs(xw[1][f], xw[2][f], xw[3][f], xv[1][f], xv[3][f], cf);
-        const Mix m = shweno_mix(P, xw[1][f], xw[2][f], xw[3][f], cf, 1);
+        double cf[6];
+        p1_coeffs_t<Q>(xw[1][f], xw[2][f], xw[3][f], xv[1][f], xv[2][f], xv[3][f], cf);
+        const Mix m = shweno_mix_t<Q>(P, xw[1][f], xw[2][f], xw[3][f], cf, 1);
         AR[f] = m.A; BR[f] = m.B; CR[f] = m.C;
       }
     }
-    char_sides<NC>(Bs, xw, xv, 0, AL, BL, CL, linL, AR, BR, CR, linR, dl, dr);
+    char_sides<NC, Q>(Bs, xw, xv, 0, AL, BL, CL, linL, AR, BR, CR, linR, dl, dr);
   } else {
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
@@ -170,8 +184,8 @@ __device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5
     // tangential order 0 first: it carries the leading-term data
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      side_out<NC, true>(ev, c0, q, 0, AL[q], BL[q], CL[q], linL, dl[q]);
-      side_out<NC, false>(ev, c0 + 1, q, 0, AR[q], BR[q], CR[q], linR, dr[q]);
+      side_out<NC, true, Q>(ev, c0, q, 0, AL[q], BL[q], CL[q], linL, dl[q]);
+      side_out<NC, false, Q>(ev, c0 + 1, q, 0, AR[q], BR[q], CR[q], linR, dr[q]);
     }
   }
   double WL[NC], WR[NC], Ws[NC];
@@ -187,12 +201,12 @@ __device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5
       if constexpr (CHAR) {
         double xw[4][NC], xv[4][NC];
         fields_at<NC>(ev, Bs, c0, k, xw, xv);
-        char_sides<NC>(Bs, xw, xv, k, AL, BL, CL, linL, AR, BR, CR, linR, dl, dr);
+        char_sides<NC, Q>(Bs, xw, xv, k, AL, BL, CL, linL, AR, BR, CR, linR, dl, dr);
       } else {
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-          side_out<NC, true>(ev, c0, q, k, AL[q], BL[q], CL[q], linL, dl[q]);
-          side_out<NC, false>(ev, c0 + 1, q, k, AR[q], BR[q], CR[q], linR, dr[q]);
+          side_out<NC, true, Q>(ev, c0, q, k, AL[q], BL[q], CL[q], linL, dl[q]);
+          side_out<NC, false, Q>(ev, c0 + 1, q, k, AR[q], BR[q], CR[q], linR, dr[q]);
         }
       }
     }
@@ -254,8 +268,10 @@ __device__ __forceinline__ double state_at(const double tc[5], double tau) {
 
 // First-pass polynomials of the cells of one tile: thread (tx, ty) of a TX x TYB block owns the
 // extended cell (bx + tx, by + ty); the 4 * NC fields of the tile plus a one-cell halo are staged
-// in shared memory `tile` (room for 16) by all nthreads threads first.
-template <int NC, int TYB>
+// in shared memory `tile` (room for 16) by all nthreads threads first.  Q: reading R1', whose
+// quintic p1 also uses the cell's own derivative average; it stores six coefficients per
+// polynomial instead of five (the scratch layout's KC).
+template <int NC, int TYB, bool Q = false>
 __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv, const double* s0,
                                             const double* s1, const uint8_t* __restrict__ flag,
                                             double* __restrict__ ycoef, double* __restrict__ xcoef,
@@ -276,6 +292,7 @@ __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv,
   const int ic = bx + tx, jr = by + ty;
   const int lx = tx + 1, ly = ty + 1;
   const int NX4 = P.nx + 4, NY2 = P.ny + 2, NY4 = P.ny + 4;
+  constexpr int KC = Q ? 6 : 5;
   if (ic <= P.nx + 1 && jr >= -1 && jr <= P.ny) {  // y-pass: {W,Y} and {V,Z} along a column
     const int nl = cell_flag(P, flag, ic, jr);
 #pragma unroll
@@ -285,13 +302,14 @@ __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv,
         const int fa = (s == 0 ? 0 : 1) * NC + q, fd = (s == 0 ? 2 : 3) * NC + q;
         const double Wm = tile[fa][ly - 1][lx], W0 = tile[fa][ly][lx], Wp = tile[fa][ly + 1][lx];
         const double vm = P.dy * tile[fd][ly - 1][lx], vp = P.dy * tile[fd][ly + 1][lx];
-        double c[5], C[5];
-        p1_coeffs(Wm, W0, Wp, vm, vp, c);
-        mix_coeffs(shweno_mix(P, Wm, W0, Wp, c, nl), Wm, W0, Wp, c, C);
+        const double v0 = Q ? P.dy * tile[fd][ly][lx] : 0.0;
+        double c[6], C[6];
+        p1_coeffs_t<Q>(Wm, W0, Wp, vm, v0, vp, c);
+        mix_coeffs_t<Q>(shweno_mix_t<Q>(P, Wm, W0, Wp, c, nl), Wm, W0, Wp, c, C);
         const double sc = s == 0 ? 1.0 : P.dx;  // x-pass derivative data: dx * avg(W_x)
 #pragma unroll
-        for (int k = 0; k < 5; ++k)
-          ycoef[((size_t)((s * NC + q) * 5 + k) * NY2 + (jr + 1)) * NX4 + (ic + 2)] = sc * C[k];
+        for (int k = 0; k < KC; ++k)
+          ycoef[((size_t)((s * NC + q) * KC + k) * NY2 + (jr + 1)) * NX4 + (ic + 2)] = sc * C[k];
       }
   }
   if (ic >= 0 && ic < P.nx && jr <= P.ny + 1) {  // x-pass: {W,V} and {Y,Z} along a row
@@ -303,20 +321,21 @@ __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv,
         const int fa = (s == 0 ? 0 : 2) * NC + q, fd = (s == 0 ? 1 : 3) * NC + q;
         const double Wm = tile[fa][ly][lx - 1], W0 = tile[fa][ly][lx], Wp = tile[fa][ly][lx + 1];
         const double vm = P.dx * tile[fd][ly][lx - 1], vp = P.dx * tile[fd][ly][lx + 1];
-        double c[5], C[5];
-        p1_coeffs(Wm, W0, Wp, vm, vp, c);
-        mix_coeffs(shweno_mix(P, Wm, W0, Wp, c, nl), Wm, W0, Wp, c, C);
+        const double v0 = Q ? P.dx * tile[fd][ly][lx] : 0.0;
+        double c[6], C[6];
+        p1_coeffs_t<Q>(Wm, W0, Wp, vm, v0, vp, c);
+        mix_coeffs_t<Q>(shweno_mix_t<Q>(P, Wm, W0, Wp, c, nl), Wm, W0, Wp, c, C);
         const double sc = s == 0 ? 1.0 : P.dy;  // y-pass derivative data: dy * avg(W_y)
 #pragma unroll
-        for (int k = 0; k < 5; ++k)
-          xcoef[((size_t)((s * NC + q) * 5 + k) * P.nx + ic) * NY4 + (jr + 2)] = sc * C[k];
+        for (int k = 0; k < KC; ++k)
+          xcoef[((size_t)((s * NC + q) * KC + k) * P.nx + ic) * NY4 + (jr + 2)] = sc * C[k];
       }
   }
 }
 
 // x-face Gauss points (slice 0..2, cell row `row`) or corner points (slice 3, corner row `row`
 // at y_{row-1/2}) of faces x_{f0-1/2} .. x_{f0+SEG-3/2}; SEG threads, smem_raw of kFaceSmem bytes.
-template <int NC, bool FLAGS, bool CHAR = false>
+template <int NC, bool FLAGS, bool CHAR = false, bool Q = false>
 __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv, const double* st,
                                            const double* __restrict__ ycoef,
                                            const uint8_t* __restrict__ flag, double* __restrict__ FX,
@@ -329,8 +348,25 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv, 
   for (int it = threadIdx.x; it < 2 * NC * SPAN; it += SEG) {
     const int col = it % SPAN, rq = it / SPAN;
     const int tcol = f0 + col;
-    double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    double e[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (tcol >= NX4) {
+    } else if constexpr (Q) {  // six coefficients per polynomial (reading R1')
+      if (slice < 3) {
+        const double* src = ycoef + ((size_t)(rq * 6) * NY2 + (row + 1)) * NX4 + tcol;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) e[k] = __ldcg(src + (size_t)k * NY2 * NX4);
+        if (slice != 1) taylor_shift_d<5>(e, slice == 0 ? -GAUSS_G : GAUSS_G);
+      } else {
+        double lo[6], hi[6];
+        const double* slo = ycoef + ((size_t)(rq * 6) * NY2 + row) * NX4 + tcol;
+        const double* shi = slo + NX4;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) { lo[k] = __ldcg(slo + (size_t)k * NY2 * NX4); hi[k] = __ldcg(shi + (size_t)k * NY2 * NX4); }
+        taylor_shift_d<5>(lo, 0.5);
+        taylor_shift_d<5>(hi, -0.5);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) e[k] = 0.5 * (lo[k] + hi[k]);
+      }
     } else if (slice < 3) {
       const double* src = ycoef + ((size_t)(rq * 5) * NY2 + (row + 1)) * NX4 + tcol;
 #pragma unroll
@@ -352,7 +388,7 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv, 
   }
   __syncthreads();
   // cell column c holds cell i = f0 + c - 2; a corner row uses the rows below and above
-  cell_mixes<NC, !CHAR>(P, ev, mt, [&](int c) {
+  cell_mixes<NC, !CHAR, Q>(P, ev, mt, [&](int c) {
     const int i = f0 + c - 2;
     return slice < 3 ? cell_flag(P, flag, i, row)
                      : (cell_flag(P, flag, i, row - 1) | cell_flag(P, flag, i, row));
@@ -372,7 +408,7 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv, 
                           fetch(P, st, 0, q, fi - 1, row, sv.t) + fetch(P, st, 0, q, fi, row, sv.t));
     }
   }
-  face_point<NC, FLAGS, CHAR>(P, ev, mt, threadIdx.x, 0, tc, Wref);
+  face_point<NC, FLAGS, CHAR, Q>(P, ev, mt, threadIdx.x, 0, tc, Wref);
   const double dt = sv.dt;
   if (slice < 3) {
     double Fh[NC], We[NC];
@@ -390,7 +426,7 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv, 
 }
 
 // y-face Gauss points (slice 0..2) of column `col`, faces y_{f0-1/2} .. y_{f0+SEG-3/2}.
-template <int NC, bool FLAGS, bool CHAR = false>
+template <int NC, bool FLAGS, bool CHAR = false, bool Q = false>
 __device__ __forceinline__ void yface_item(const Params& P, const StepView& sv, const double* st,
                                            const double* __restrict__ xcoef,
                                            const uint8_t* __restrict__ flag, double* __restrict__ FY,
@@ -403,18 +439,23 @@ __device__ __forceinline__ void yface_item(const Params& P, const StepView& sv, 
   for (int it = threadIdx.x; it < 2 * NC * SPAN; it += SEG) {
     const int r = it % SPAN, rq = it / SPAN;
     const int trow = f0 + r;
-    double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    double e[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (trow < NY4) {
-      const double* src = xcoef + ((size_t)(rq * 5) * P.nx + col) * NY4 + trow;
+      constexpr int KC = Q ? 6 : 5;
+      const double* src = xcoef + ((size_t)(rq * KC) * P.nx + col) * NY4 + trow;
 #pragma unroll
-      for (int k = 0; k < 5; ++k) e[k] = __ldcg(src + (size_t)k * P.nx * NY4);
-      if (slice != 1) taylor_shift(e, slice == 0 ? -GAUSS_G : GAUSS_G, 4);
+      for (int k = 0; k < KC; ++k) e[k] = __ldcg(src + (size_t)k * P.nx * NY4);
+      if constexpr (Q) {
+        if (slice != 1) taylor_shift_d<5>(e, slice == 0 ? -GAUSS_G : GAUSS_G);
+      } else {
+        if (slice != 1) taylor_shift(e, slice == 0 ? -GAUSS_G : GAUSS_G, 4);
+      }
     }
 #pragma unroll
     for (int k = 0; k < 5; ++k) ev[rq][k][r] = e[k];
   }
   __syncthreads();
-  cell_mixes<NC, !CHAR>(P, ev, mt, [&](int c) { return cell_flag(P, flag, col, f0 + c - 2); });
+  cell_mixes<NC, !CHAR, Q>(P, ev, mt, [&](int c) { return cell_flag(P, flag, col, f0 + c - 2); });
   __syncthreads();
   const int fj = f0 + threadIdx.x;  // face y_{fj-1/2}
   if (fj > P.ny) return;
@@ -425,7 +466,7 @@ __device__ __forceinline__ void yface_item(const Params& P, const StepView& sv, 
     for (int q = 0; q < NC; ++q)
       Wref[q] = 0.5 * (fetch(P, st, 0, q, col, fj - 1, sv.t) + fetch(P, st, 0, q, col, fj, sv.t));
   }
-  face_point<NC, FLAGS, CHAR>(P, ev, mt, threadIdx.x, 1, tc, Wref);
+  face_point<NC, FLAGS, CHAR, Q>(P, ev, mt, threadIdx.x, 1, tc, Wref);
   double Gh[NC], We[NC];
   lobatto<NC>(tc, sv.dt, P.gamma, 1, Gh, We);
 #pragma unroll

@@ -34,7 +34,7 @@ class shweno_bc(ctypes.Structure):
 
 class shweno_opts(ctypes.Structure):
     _fields_ = [("flag_mode", ctypes.c_int32), ("eps", ctypes.c_double), ("gam", ctypes.c_double * 3),
-                ("charwise", ctypes.c_int32)]
+                ("charwise", ctypes.c_int32), ("quintic", ctypes.c_int32)]
 
 
 class ShwenoError(RuntimeError):
@@ -320,9 +320,9 @@ def make_bc(kinds, inflow=None):
     return b
 
 
-def make_opts(flag_mode=0, eps=1e-6, gam=(0.994, 0.003, 0.003), charwise=False):
+def make_opts(flag_mode=0, eps=1e-6, gam=(0.994, 0.003, 0.003), charwise=False, quintic=False):
     o = shweno_opts()
-    o.flag_mode, o.eps, o.charwise = flag_mode, eps, 1 if charwise else 0
+    o.flag_mode, o.eps, o.charwise, o.quintic = flag_mode, eps, 1 if charwise else 0, 1 if quintic else 0
     for k in range(3):
         o.gam[k] = gam[k]
     return o
@@ -333,11 +333,11 @@ class Solver:
     or torch CUDA tensors (device)."""
 
     def __init__(self, dim, eq, nx, ny=1, domain=(0.0, 1.0, 0.0, 1.0), bc=(0, 0, 0, 0), gamma=1.4,
-                 inflow=None, flag_mode=0, eps=1e-6, stream=0, charwise=False):
+                 inflow=None, flag_mode=0, eps=1e-6, stream=0, charwise=False, quintic=False):
         self.dim, self.eq, self.nx, self.ny = dim, eq, nx, (ny if dim == 2 else 1)
         self.ncomp = 1 if eq == BURGERS else (3 if dim == 1 else 4)
         self.h = shweno_create(make_grid(dim, eq, nx, ny, *domain), gamma, make_bc(bc, inflow),
-                               make_opts(flag_mode, eps, charwise=charwise), stream)
+                               make_opts(flag_mode, eps, charwise=charwise, quintic=quintic), stream)
 
     @property
     def shape(self):

@@ -60,9 +60,9 @@ def check(g, o, keys, shocked, what="", wl=None):
                             f"{(rel_l1 if shocked else rel_linf)(g[k], o[k]):.3e} (ratio to tolerance {err:.2f})")
 
 
-def steps_both(wl, dts, flag=None, flag_mode=0, linear=False, t0=0.0, charwise=False):
+def steps_both(wl, dts, flag=None, flag_mode=0, linear=False, t0=0.0, charwise=False, quintic=False):
     """Fixed-dt steps on both sides; returns (gpu_state, oracle_state)."""
-    sol = solver_of(wl, flag_mode=flag_mode, charwise=charwise)
+    sol = solver_of(wl, flag_mode=flag_mode, charwise=charwise, quintic=quintic)
     sol.set_state(wl.state, t0)
     if flag is not None:
         sol.set_flags(flag)
@@ -70,7 +70,7 @@ def steps_both(wl, dts, flag=None, flag_mode=0, linear=False, t0=0.0, charwise=F
         sol.step(dt)
     g = sol.get_state()
     sol.close()
-    P = problem_of(wl, linear=linear, charwise=charwise)
+    P = problem_of(wl, linear=linear, charwise=charwise, quintic=quintic)
     o = wl.state
     t = t0
     for dt in dts:
@@ -79,14 +79,14 @@ def steps_both(wl, dts, flag=None, flag_mode=0, linear=False, t0=0.0, charwise=F
     return g, o
 
 
-def run_both(wl, t_final, flag=None, flag_mode=0, linear=False, charwise=False):
-    sol = solver_of(wl, flag_mode=flag_mode, charwise=charwise)
+def run_both(wl, t_final, flag=None, flag_mode=0, linear=False, charwise=False, quintic=False):
+    sol = solver_of(wl, flag_mode=flag_mode, charwise=charwise, quintic=quintic)
     sol.set_state(wl.state)
     if flag is not None:
         sol.set_flags(flag)
     t, n = sol.run(t_final, wl.cfl)
     g = sol.get_state()
     sol.close()
-    P = problem_of(wl, linear=linear, charwise=charwise)
+    P = problem_of(wl, linear=linear, charwise=charwise, quintic=quintic)
     o, n_o, t_o = O.run(P, wl.state, t_final, wl.cfl, flag=flag)
     return g, o, (t, n), (t_o, n_o)
