@@ -51,7 +51,7 @@ typedef enum { SHWENO_BURGERS = 0, SHWENO_EULER = 1 } shweno_eq;
 
 /* Boundary conditions (Section 5 examples).  Ghost cells are never stored; they are mapped
  * on load.  OUTFLOW copies every cell quantity of the boundary cell (zero-order extrapolation,
- * the "non-reflecting"/outflow sides of Examples 5.3, 5.9, 5.10).  REFLECTIVE mirrors the
+ * the non-reflecting (outflow) sides of Examples 5.3, 5.9, 5.10).  REFLECTIVE mirrors the
  * state with the normal momentum and the derivatives normal to the wall changing sign
  * (Example 5.6).  INFLOW imposes the conserved state inflow[side] with zero derivatives.
  * DMR_BOTTOM / DMR_TOP are the lower and upper sides of the double Mach reflection problem

@@ -387,7 +387,8 @@ double wave_scale(const Problem& P, const double* Ws, double uL, double uR) {
 // series are the Cauchy products of the coefficient arrays.  The PDE W_t = -F_x - G_y says
 // (k+1) a[m][n][k+1] = -(m+1) f[m+1][n][k] - (n+1) g[m][n+1][k]; the time slices are filled one
 // after another, each from fluxes evaluated on the slices already known.  This gives the full
-// nonlinear expressions of Eq. (2.6) and of Section 3.1 ("and so on") to fourth order.
+// nonlinear expressions of Eq. (2.6) and of Section 3.1 (written out there only for the first
+// derivatives) to fourth order.
 // ----------------------------------------------------------------------------------------
 const int ORD = 4;
 struct Ser { double c[5][5][5]; };
@@ -872,7 +873,7 @@ void yface(const State& S, int i, int j, double dt, double* Gs, double* Ws) {
 }
 // State at t_{n+1} at the corner (i+1/2, j+1/2): the y-direction traces of rows j (eta = +1/2)
 // and j+1 (eta = -1/2) are averaged, then one x-direction generalised Riemann problem is solved
-// and evaluated at tau = dt (the paper says only "in a similar way", end of Section 3.3).
+// and evaluated at tau = dt (the paper gives no detail for the corners, end of Section 3.3).
 void corner(const State& S, int i, int j, double dt, double* We) {
   const Problem& P = *S.P;
   const int nc = ncomp(P);
