@@ -163,7 +163,8 @@ class Gen:
         return " + ".join(terms)
 
     def quotient(self, A, B, name, m, n, k):
-        """name = A / B; name[g] = (A[g] - sum_{0 < b <= g} B[b] name[g - b]) / B[0]."""
+        """name = A / B; name[g] = (A[g] - sum_{0 < b <= g} B[b] name[g - b]) / B[0], the sum
+        subtracted term by term."""
         a = self.var(A, m, n, k)
         terms = []
         for p, q, t in self.sub_indices(m, n, k):
@@ -175,7 +176,8 @@ class Gen:
                 terms.append(f"{b} * {c}")
         num = a if a is not None else "0.0"
         if terms:
-            num = f"({num} - ({' + '.join(terms)}))"
+            # a - t1 - t2 - ... left to right: every step contracts to one fused multiply-add
+            num = "(" + num + "".join(f" - {t}" for t in terms) + ")"
             self.flops += 2 * len(terms)
         self.flops += 1
         return f"{num} * inv_r0"
