@@ -243,14 +243,16 @@ shweno_status shweno_batch_create(shweno_handle* const* hs, int n, void* cuda_st
 shweno_status shweno_batch_run(shweno_batch* b, const double* t_final, double cfl, int64_t max_steps,
                                shweno_status* per_problem);
 
-/* Autotuner: times the candidate launch shapes (1D tile of 128..1024 cells, 1 or 2 CTAs per SM)
- * on trial_steps steps of the actual problems, restoring every state afterwards, and keeps the
- * fastest; the choice is written to tile1d_out / ctas_per_sm_out (may be NULL). */
+/* Autotuner: times the candidate launch shapes (1D tile of 128..1024 cells; 1 or 2 CTAs per SM,
+ * or 2..4 when every problem is 1D and the lighter 1D-only kernel runs) on trial_steps steps of
+ * the actual problems, restoring every state afterwards, and keeps the fastest; the choice is
+ * written to tile1d_out / ctas_per_sm_out (may be NULL). */
 shweno_status shweno_batch_autotune(shweno_batch* b, const double* t_final, double cfl,
                                     int64_t trial_steps, int* tile1d_out, int* ctas_per_sm_out);
 
 /* Sets the launch shape by hand and the bound of the empty-queue wait (values <= 0 keep the
- * current setting).  tile1d: power of 2 in [128, 1024]; ctas_per_sm: 1 or 2. */
+ * current setting).  tile1d: power of 2 in [128, 1024]; ctas_per_sm: 1 or 2 (1..4 for a batch
+ * of 1D problems only).  Errors: INVALID (out of range). */
 shweno_status shweno_batch_set(shweno_batch* b, int tile1d, int ctas_per_sm, int64_t spin_limit);
 
 shweno_status shweno_batch_destroy(shweno_batch* b);

@@ -64,6 +64,8 @@ struct BatchCtl {
 
 constexpr size_t kBatchSmem = kFaceSmem > sizeof(double) * 16 * (TYB + 2) * (TX + 2) ?
                               kFaceSmem : sizeof(double) * 16 * (TYB + 2) * (TX + 2);
+constexpr size_t kBatchSmem1D = sizeof(double) * 2 * 3 * (1024 + 1);  // F-hat and W(t+dt) of a tile
+static_assert(kBatchSmem1D <= kBatchSmem, "1D tiles fit the 2D batch's shared memory");
 
 __device__ __forceinline__ long long enc(int p, int ph, long long idx) {
   return ((long long)p << 40) | ((long long)ph << 36) | idx;
@@ -99,11 +101,15 @@ __device__ bool begin_problem_step(const BatchProblem& B) {
 }
 
 // ------------------------------------------------------------------ the work of one item
+// HAS2D = false: a batch of 1D problems only; the 2D items are left out of the kernel, which
+// then needs about half the registers and runs more CTAs per SM.
+template <bool HAS2D>
 __device__ void do_item(const BatchProblem& B, int kind, long long idx, unsigned char* smem) {
   const Params& P = B.P;
   Ctl* ctl = B.ctl;
   const StepView sv = step_view(ctl);
   __shared__ double red[BT / 32];
+  if (!HAS2D) kind = PH_TILE1D;
   switch (kind) {
     case PH_TILE1D: {  // 1D: faces of the tile into shared memory, then the cells' update
       const int c0 = (int)idx * B.tile1d;
@@ -135,6 +141,8 @@ __device__ void do_item(const BatchProblem& B, int kind, long long idx, unsigned
       block_max_rate(rate, &ctl->rate_next, red);
       break;
     }
+  }
+  if constexpr (HAS2D) switch (kind) {
     case PH_INFER: {
       float* p = reinterpret_cast<float*>(smem);
       load_params(B.net, p);
@@ -216,7 +224,8 @@ __device__ void do_item(const BatchProblem& B, int kind, long long idx, unsigned
 }
 
 // ------------------------------------------------------------------ persistent kernel
-__global__ void __launch_bounds__(BT) batch_kernel(const BatchProblem* __restrict__ probs, int* pstate,
+template <bool HAS2D>
+__global__ void __launch_bounds__(BT, HAS2D ? 1 : 4) batch_kernel(const BatchProblem* __restrict__ probs, int* pstate,
                                                    BatchCtl* bc, long long* items, unsigned long long* seq,
                                                    unsigned long long mask, long long spin_limit) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -249,7 +258,7 @@ __global__ void __launch_bounds__(BT) batch_kernel(const BatchProblem* __restric
     const int p = (int)(item >> 40), ph = (int)((item >> 36) & 15);
     const long long idx = item & ((1ll << 36) - 1);
     const BatchProblem& B = probs[p];
-    do_item(B, B.phase_kind[ph], idx, smem);
+    do_item<HAS2D>(B, B.phase_kind[ph], idx, smem);
     __threadfence();  // this thread's results visible device-wide before the item counts as done
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -364,6 +373,7 @@ struct shweno_batch {
   bool own_stream = false;
   int tile1d = 512;
   int ctas_per_sm = 2;
+  bool has2d = true;  // false: every problem is 1D (the lighter kernel, up to 4 CTAs per SM)
   int grid = 0;
   long long spin_limit = 4000000;  // x ~256 ns sleeps: about a second
   std::string err;
@@ -444,6 +454,9 @@ shweno_status shweno_batch_create(shweno_handle* const* hs, int n, void* cuda_st
       return SHWENO_E_STATE;
     }
   }
+  b->has2d = false;
+  for (int p = 0; p < n; ++p) b->has2d |= b->views[p].P.dim == 2;
+  if (!b->has2d) b->ctas_per_sm = 4;
   if (cuda_stream) b->stream = (cudaStream_t)cuda_stream;
   else { cudaStreamCreate(&b->stream); b->own_stream = true; }
   int dev = 0, sms = 0;
@@ -483,7 +496,8 @@ shweno_status shweno_batch_create(shweno_handle* const* hs, int n, void* cuda_st
     return SHWENO_E_NOMEM;
   }
   cudaMemcpy(b->chunk0, ch.data(), n * sizeof(int), cudaMemcpyHostToDevice);
-  cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem);
+  cudaFuncSetAttribute(batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem);
+  cudaFuncSetAttribute(batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem1D);
   *out = b;
   return SHWENO_OK;
 }
@@ -520,8 +534,12 @@ void enqueue_batch(shweno_batch* b, double cfl) {
       b->bc, n, b->seq, cap, b->pstate);
   batch_rate_kernel<<<b->nchunks, 256, 0, b->stream>>>(b->probs, b->chunk0, n);
   batch_seed_kernel<<<(n + 127) / 128, 128, 0, b->stream>>>(b->probs, n, b->bc, b->items, b->seq, cap - 1);
-  batch_kernel<<<b->grid, BT, kBatchSmem, b->stream>>>(b->probs, b->pstate, b->bc, b->items, b->seq, cap - 1,
-                                                        b->spin_limit);
+  if (b->has2d)
+    batch_kernel<true><<<b->grid, BT, kBatchSmem, b->stream>>>(b->probs, b->pstate, b->bc, b->items, b->seq,
+                                                               cap - 1, b->spin_limit);
+  else
+    batch_kernel<false><<<b->grid, BT, kBatchSmem1D, b->stream>>>(b->probs, b->pstate, b->bc, b->items, b->seq,
+                                                                  cap - 1, b->spin_limit);
 }
 
 shweno_status run_once(shweno_batch* b, const double* t_final, double cfl, int64_t max_steps, bool graph) {
@@ -631,7 +649,7 @@ shweno_status shweno_batch_autotune(shweno_batch* b, const double* t_final, doub
     cudaStreamSynchronize(b->stream);
   };
   std::vector<int> tiles = any1d ? std::vector<int>{128, 256, 512, 1024} : std::vector<int>{b->tile1d};
-  std::vector<int> occ = {1, 2};
+  std::vector<int> occ = b->has2d ? std::vector<int>{1, 2} : std::vector<int>{2, 3, 4};
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -678,7 +696,8 @@ shweno_status shweno_batch_set(shweno_batch* b, int tile1d, int ctas_per_sm, int
     b->tile1d = tile1d;
   }
   if (ctas_per_sm > 0) {
-    if (ctas_per_sm > 2) return bfail(b, SHWENO_E_INVALID, "ctas_per_sm must be 1 or 2");
+    if (ctas_per_sm > (b->has2d ? 2 : 4))
+      return bfail(b, SHWENO_E_INVALID, "ctas_per_sm must be 1..2 (1..4 for a batch of 1D problems)");
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

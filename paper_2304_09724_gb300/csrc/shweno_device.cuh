@@ -209,12 +209,12 @@ __device__ __forceinline__ Mix shweno_mix(const Params& P, double Wm, double W0,
   const double b2 = d2 * d2, b3 = d3 * d3;
   double tau = 0.5 * (fabs(b1 - b2) + fabs(b1 - b3));
   tau = tau * tau;
-  // the three 1/(b_l + eps) from one division
+  // w_l is proportional to gam_l (1 + tau/e_l) = gam_l (e_l + tau) / e_l; scaling all three by
+  // e1 e2 e3 leaves the normalised weights unchanged and leaves one division (the normalisation)
   const double e1 = b1 + P.eps, e2 = b2 + P.eps, e3 = b3 + P.eps;
-  const double e12 = e1 * e2, r = 1.0 / (e12 * e3);
-  const double w1 = P.gam[0] * (1.0 + tau * (e2 * e3 * r));
-  const double w2 = P.gam[1] * (1.0 + tau * (e1 * e3 * r));
-  const double w3 = P.gam[2] * (1.0 + tau * (e12 * r));
+  const double w1 = P.gam[0] * (e1 + tau) * (e2 * e3);
+  const double w2 = P.gam[1] * (e2 + tau) * (e1 * e3);
+  const double w3 = P.gam[2] * (e3 + tau) * (e1 * e2);
   const double inv = 1.0 / (w1 + w2 + w3);
   const double A = w1 * inv * P.igam[0];
   return Mix{A, w2 * inv - A * P.gam[1], w3 * inv - A * P.gam[2]};
@@ -267,10 +267,9 @@ __device__ __forceinline__ Mix shweno_mix_t(const Params& P, double Wm, double W
     double tau = 0.5 * (fabs(b1 - b2) + fabs(b1 - b3));
     tau = tau * tau;
     const double e1 = b1 + P.eps, e2 = b2 + P.eps, e3 = b3 + P.eps;
-    const double e12 = e1 * e2, r = 1.0 / (e12 * e3);
-    const double w1 = P.gam[0] * (1.0 + tau * (e2 * e3 * r));
-    const double w2 = P.gam[1] * (1.0 + tau * (e1 * e3 * r));
-    const double w3 = P.gam[2] * (1.0 + tau * (e12 * r));
+    const double w1 = P.gam[0] * (e1 + tau) * (e2 * e3);
+    const double w2 = P.gam[1] * (e2 + tau) * (e1 * e3);
+    const double w3 = P.gam[2] * (e3 + tau) * (e1 * e2);
     const double inv = 1.0 / (w1 + w2 + w3);
     const double A = w1 * inv * P.igam[0];
     return Mix{A, w2 * inv - A * P.gam[1], w3 * inv - A * P.gam[2]};

@@ -147,3 +147,33 @@ def test_wait_that_runs_out_reports_timeout_and_handles_stay_usable():
             status = e.status
         same((s.get_state(), s.time()), solo(wl, 0.05), wl, status)
         s.close()
+
+
+def test_1d_only_batch_runs_up_to_four_ctas_per_sm():
+    """A batch of 1D problems runs the lighter 1D-only kernel: 3 and 4 CTAs per SM give what the
+    handles give on their own; a batch with a 2D problem refuses more than 2."""
+    wls = [WL.random_riemann1d(s, nx=n) for s, n in zip(range(40, 44), (300, 1000, 77, 2048))]
+    for occ in (3, 4):
+        sols = []
+        for wl in wls:
+            s = U.solver_of(wl)
+            s.set_state(wl.state)
+            sols.append(s)
+        b = S.Batch(sols)
+        b.set(ctas_per_sm=occ)
+        st, per = b.run([0.03] * len(wls), wls[0].cfl)
+        outs = [(s.get_state(), s.time()) for s in sols]
+        b.close()
+        for s in sols:
+            s.close()
+        for wl, o, p in zip(wls, outs, per):
+            same(o, solo(wl, 0.03), wl, p)
+    wl2 = WL.riemann2d(16, WL.LAX_LIU_SHOCKS)
+    s2 = U.solver_of(wl2)
+    s2.set_state(wl2.state)
+    b = S.Batch([s2])
+    with pytest.raises(S.ShwenoError) as e:
+        b.set(ctas_per_sm=3)
+    assert e.value.status == S.E_INVALID
+    b.close()
+    s2.close()
