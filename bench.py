@@ -36,9 +36,9 @@ FP64_MEASURED_TFLOPS = 1.1935  # DFMA microbenchmark on this machine's GB300 (all S
 # FP64 operations (DFMA counted as 2) per x-face point of xface2d, from the ncu instruction
 # counters of the committed kernel (profiles/xface2d_vortex512.md), and its DRAM bytes per point
 # from the same capture (512^2; traffic grows in proportion to the points).
-FLOPS_PER_XFACE_POINT = 5888
-FP64_INST_PER_XFACE_POINT = 3411  # DFMA + DMUL + DADD thread instructions (each one pipe slot)
-DRAM_BYTES_PER_XFACE_POINT = 344.4
+FLOPS_PER_XFACE_POINT = 5828
+FP64_INST_PER_XFACE_POINT = 3376  # DFMA + DMUL + DADD thread instructions (each one pipe slot)
+DRAM_BYTES_PER_XFACE_POINT = 343.9
 BYTES_PER_CELL_UPDATE = 256  # 16 doubles read + 16 written per cell (ideal reuse)
 
 

@@ -203,10 +203,27 @@ __device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5
         fields_at<NC>(ev, Bs, c0, k, xw, xv);
         char_sides<NC, Q>(Bs, xw, xv, k, AL, BL, CL, linL, AR, BR, CR, linR, dl, dr);
       } else {
+        if constexpr (FLAGS) {
+          // the flagged instantiation reloads the weights from shared memory for every order
+          // (measured: 3 % faster for it; the plain one is 3 % faster keeping them in registers)
+          const volatile double* vA = &mt.A[0][0];
+          const volatile double* vB = &mt.B[0][0];
+          const volatile double* vC = &mt.C[0][0];
 #pragma unroll
-        for (int q = 0; q < NC; ++q) {
-          side_out<NC, true, Q>(ev, c0, q, k, AL[q], BL[q], CL[q], linL, dl[q]);
-          side_out<NC, false, Q>(ev, c0 + 1, q, k, AR[q], BR[q], CR[q], linR, dr[q]);
+          for (int q = 0; q < NC; ++q) {
+            const double aL = linL ? 1.0 : vA[q * SPAN + c0 + 1], bL = linL ? 0.0 : vB[q * SPAN + c0 + 1];
+            const double cL = linL ? 0.0 : vC[q * SPAN + c0 + 1];
+            const double aR = linR ? 1.0 : vA[q * SPAN + c0 + 2], bR = linR ? 0.0 : vB[q * SPAN + c0 + 2];
+            const double cR = linR ? 0.0 : vC[q * SPAN + c0 + 2];
+            side_out<NC, true, Q>(ev, c0, q, k, aL, bL, cL, linL, dl[q]);
+            side_out<NC, false, Q>(ev, c0 + 1, q, k, aR, bR, cR, linR, dr[q]);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < NC; ++q) {
+            side_out<NC, true, Q>(ev, c0, q, k, AL[q], BL[q], CL[q], linL, dl[q]);
+            side_out<NC, false, Q>(ev, c0 + 1, q, k, AR[q], BR[q], CR[q], linR, dr[q]);
+          }
         }
       }
     }
