@@ -433,6 +433,60 @@ def bench_gpu(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_learned_run(args):
+    """Opt-in suite (--suite learned-run): the double Mach reflection (Example 5.10) run to its
+    final time T = 0.2 with the always-nonlinear weights and with the learned flag, at
+    --dmr-nx x --dmr-nx/4 cells: wall time of each full run (CUDA events, device-side time loop),
+    steps, the learned form's flagged fraction at the end and its relative L1 deviation from the
+    plain solution over all cell averages at T."""
+    import numpy as np
+    import torch
+
+    from paper_2304_09724_gb300 import flagnet as F
+    from paper_2304_09724_gb300 import shweno as S
+    from paper_2304_09724_gb300 import workloads as WL
+
+    torch.cuda.set_device(0)
+    nx = args.dmr_nx
+    wl = WL.dmr(nx, nx // 4)
+    net = F.load()
+    out = {"suite": "learned-run", "workload": f"double Mach reflection {nx}x{nx // 4}, T = 0.2, CFL {CFL}",
+           "dtype": "f64", "data": "synthetic"}
+    states = {}
+    for mode in ("plain", "learned"):
+        stream = torch.cuda.Stream()
+        sol = S.Solver(2, S.EULER, wl.nx, wl.ny, wl.domain, wl.bc, inflow=wl.inflow,
+                       flag_mode=2 if mode == "learned" else 0, stream=stream.cuda_stream)
+        sol.set_state({k: torch.from_numpy(np.array(v)).cuda() for k, v in wl.state.items()})
+        if mode == "learned":
+            S.shweno_set_flag_net(sol.h, torch.from_numpy(net[0]).cuda(), net[1])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        status = "ok"
+        try:
+            t, n = sol.run(0.2, CFL)
+        except S.ShwenoError as e:
+            status = "nonphysical" if e.status == S.E_NONPHYSICAL else str(e)
+            t, n = sol.time()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1000.0
+        res = {"status": status, "t": t, "steps": n, "seconds": sec,
+               "cell_updates_per_s": wl.nx * wl.ny * n / sec}
+        if mode == "learned":
+            fl = np.empty((wl.ny, wl.nx), dtype=np.uint8)
+            S.shweno_get_flags(sol.h, fl)
+            res["flagged_fraction_at_T"] = float(fl.mean())
+        states[mode] = sol.get_state()
+        sol.close()
+        out[mode] = res
+    a, b = states["plain"]["W"], states["learned"]["W"]
+    out["rel_l1_learned_vs_plain_W"] = float(np.sum(np.abs(b - a)) / np.sum(np.abs(a)))
+    out["speedup"] = out["learned"]["cell_updates_per_s"] / out["plain"]["cell_updates_per_s"]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -444,11 +498,14 @@ def main():
     ap.add_argument("--ref-window", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--suite", default="main", choices=["main", "batched"])
+    ap.add_argument("--suite", default="main", choices=["main", "batched", "learned-run"])
+    ap.add_argument("--dmr-nx", type=int, default=2048, help="learned-run: DMR mesh is N x N/4")
     ap.add_argument("--c5-problems", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
+    elif args.suite == "learned-run":
+        bench_learned_run(args)
     elif args.suite == "batched":
         bench_batched(args)
     else:
