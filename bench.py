@@ -496,6 +496,40 @@ def bench_learned_run(args):
     print(json.dumps(out), flush=True)
 
 
+def bench_euler1d(args):
+    """Opt-in suite (--suite euler1d): one large 1D Euler problem (--n1d cells, seeded smooth
+    periodic data, fixed dt = 0.2 / n), `warmup` then `steps` steps through shweno_step: cell-updates/s
+    from CUDA events and the per-kernel split."""
+    import torch
+
+    from paper_2304_09724_gb300 import shweno as S
+    from paper_2304_09724_gb300 import workloads as WL
+
+    torch.cuda.set_device(0)
+    n = args.n1d
+    W, V = WL.random_smooth_1d(3, n)
+    sol = S.Solver(1, S.EULER, n, domain=(0.0, 1.0, 0.0, 1.0), bc=(0, 0))
+    sol.set_state({"W": W, "V": V})
+    dt = 0.2 / n
+    for _ in range(args.warmup):
+        sol.step(dt)
+    torch.cuda.synchronize()
+    S.shweno_set_timing(sol.h, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sol.step(dt)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kms, k = S.shweno_get_timing(sol.h)
+    sol.close()
+    print(json.dumps({"suite": "euler1d", "cells": n, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": ms / args.steps, "cell_updates_per_s": n * args.steps / (ms / 1000.0),
+                      "kernels_ms_per_step": {a: b / max(k, 1) for a, b in kms.items()},
+                      "dtype": "f64", "data": "synthetic"}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -507,12 +541,15 @@ def main():
     ap.add_argument("--ref-window", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--suite", default="main", choices=["main", "batched", "learned-run"])
+    ap.add_argument("--suite", default="main", choices=["main", "batched", "learned-run", "euler1d"])
+    ap.add_argument("--n1d", type=int, default=4194304, help="euler1d: cells of the 1D problem")
     ap.add_argument("--dmr-nx", type=int, default=1024, help="learned-run: DMR mesh is N x N/4")
     ap.add_argument("--c5-problems", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
+    elif args.suite == "euler1d":
+        bench_euler1d(args)
     elif args.suite == "learned-run":
         bench_learned_run(args)
     elif args.suite == "batched":
