@@ -106,6 +106,41 @@ def test_order_euler1d_example_5_2():
     assert math.log2(errs[40] / errs[80]) > 4.7
 
 
+def test_table_5_2_error_magnitudes_l1_and_linf():
+    """Example 5.2 is run as printed (T = 10; CFL 0.6 of the configurations): the oracle's density
+    errors fall within 0.8-1.5x of Table 5.2 in both norms at every N (measured 1.10-1.15x)."""
+    tab = paper_table()
+    for n in (20, 40, 80):
+        wl = WL.euler1d_sine(n)
+        st, _, _ = run(wl)
+        e = st["W"][0] - wl.exact(wl.t_final)[0]
+        for norm, val in (("L1", np.mean(np.abs(e))), ("Linf", np.max(np.abs(e)))):
+            assert 0.8 < val / tab[("5.2", norm, n)] < 1.5, (norm, n, val)
+
+
+def test_table_5_1_linf_magnitudes():
+    """Example 5.1 (Table 5.1 used CFL 0.9, the configurations 0.6): L-infinity errors within
+    0.05-5x of the table and the same order."""
+    tab = paper_table()
+    errs = {}
+    for n in (40, 80, 160):
+        wl = WL.burgers_sine(n)
+        st, _, _ = run(wl)
+        errs[n] = float(np.max(np.abs(st["W"][0] - wl.exact(wl.t_final)[0])))
+        assert 0.05 < errs[n] / tab[("5.1", "Linf", n)] < 5.0
+    assert math.log2(errs[80] / errs[160]) > 4.3
+
+
+def test_table_5_3_magnitude_example_5_7():
+    """Example 5.7 at 20 x 20 to T = 1 as printed: density L1 error within 0.7-1.4x of Table 5.3
+    (measured 1.005x)."""
+    tab = paper_table()
+    wl = WL.euler2d_sine(20)
+    st, _, _ = run(wl, t_final=1.0)
+    val = float(np.mean(np.abs(st["W"][0] - wl.exact(1.0)[0])))
+    assert 0.7 < val / tab[("5.3", "L1", 20)] < 1.4, val
+
+
 def test_order_euler2d_example_5_7():
     errs = {}
     for n in (10, 20):
