@@ -116,3 +116,26 @@ def test_sod_charwise_against_exact():
         assert rho.min() > 0.125 * 0.97 and rho.max() < 1.0 * 1.03
     assert errs[200] < 0.75 * errs[100]
     assert errs[200] < 4e-3
+
+
+def test_2d_reflective_wall_along_y_equals_1d_charwise():
+    """A shock running into a reflective wall along y in 2D (data depending on y only) gives the
+    1D characteristic-wise scheme with the same wall, on every column."""
+    n, m = 60, 4
+    wl1 = WL.riemann1d(n, (3.0, -1.5, 5.0), (1.0, -1.5, 1.0), xs=0.5, bc=(WL.REFLECTIVE, WL.OUTFLOW))
+    W1, V1 = wl1.state["W"], wl1.state["V"]
+    rho, mom, E = W1
+    zero = np.zeros_like(rho)
+    W2 = np.stack([np.repeat(c[:, None], m, axis=1) for c in (rho, zero, mom, E)])
+    D2 = np.stack([np.repeat(c[:, None], m, axis=1) for c in (V1[0], zero, V1[1], V1[2])])
+    s2 = {"W": W2, "V": np.zeros_like(W2), "Y": D2, "Z": np.zeros_like(W2)}
+    P1 = O.make_problem(1, WL.EULER, n, x0=0.0, x1=1.0, bc=(WL.REFLECTIVE, WL.OUTFLOW), charwise=True)
+    P2 = O.make_problem(2, WL.EULER, m, n, 0.0, 0.2, 0.0, 1.0, bc=(0, 0, WL.REFLECTIVE, WL.OUTFLOW),
+                        charwise=True)
+    s1 = wl1.state
+    for _ in range(40):
+        s1 = O.step(P1, s1, 0.002)
+        s2 = O.step(P2, s2, 0.002)
+    for q2, q1 in ((0, 0), (2, 1), (3, 2)):
+        for c in range(m):
+            np.testing.assert_allclose(s2["W"][q2][:, c], s1["W"][q1], rtol=1e-12, atol=1e-12)
