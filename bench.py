@@ -32,12 +32,13 @@ CFL = 0.6
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP64_SLOTS_PER_S = 152 * 2 * 2.070e9  # FP64 thread instructions per second (DFMA, DMUL, DADD alike)
-FP64_MEASURED_TFLOPS = 1.1935  # DFMA microbenchmark on this machine's GB300 (all SMs busy)
-# FP64 operations (DFMA counted as 2) per x-face point of xface2d, from the ncu instruction
-# counters of the committed kernel (profiles/xface2d_vortex512.md), and its DRAM bytes per point
-# from the same capture (512^2; traffic grows in proportion to the points).
-FLOPS_PER_XFACE_POINT = 5828
-FP64_INST_PER_XFACE_POINT = 3376  # DFMA + DMUL + DADD thread instructions (each one pipe slot)
+# FP64 operations (DFMA counted as 2) and FP64 thread instructions (DFMA + DMUL + DADD, each one
+# pipe slot) per x-face point of xface2d, from the ncu instruction counters of the committed
+# kernel on the 2048^2 launch (profiles/fp64_pipe_vortex2048.md; 1 % more per point at 512^2,
+# where more of the 128-face segments are ragged), and its DRAM bytes per point from the 512^2
+# capture (profiles/xface2d_vortex512.md; traffic grows in proportion to the points).
+FLOPS_PER_XFACE_POINT = 5766.6
+FP64_INST_PER_XFACE_POINT = 3333.9
 DRAM_BYTES_PER_XFACE_POINT = 343.9
 BYTES_PER_CELL_UPDATE = 256  # 16 doubles read + 16 written per cell (ideal reuse)
 
@@ -389,6 +390,8 @@ def bench_gpu(args):
     state_bytes = sum(v.numel() * 8 for v in host_in.values())
     assert np.isfinite(host_out["W"].numpy()).all()
     sol.close()
+    # the FP64 rate this GPU reaches on independent fused multiply-add chains (outside the timing)
+    fp64_tf, fp64_per_clk = S.shweno_fp64_probe(S.FP64_FMA, 8, 1 << 16)
 
     if rank != 0:
         return
@@ -398,6 +401,8 @@ def bench_gpu(args):
     dom_ms = kernel_ms[dom] / max(timed_steps, 1)
     # x-face kernel: (n+1) faces x n rows x 3 Gauss points + (n+1)^2 corner points per launch
     xpoints = 3 * (n + 1) * n + (n + 1) * (n + 1)
+    sm_hz = (clocks.get("sm_mhz") or 2070.0) * 1e6
+    inst_per_clk = FP64_INST_PER_XFACE_POINT * xpoints / (dom_ms / 1000.0) / (152 * sm_hz)
     roof = None
     if dom == "xface2d" and FLOPS_PER_XFACE_POINT:
         flops = FLOPS_PER_XFACE_POINT * xpoints
@@ -406,7 +411,12 @@ def bench_gpu(args):
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": DRAM_BYTES_PER_XFACE_POINT * xpoints,
                 "flops_per_launch": flops, "launch_ms": dom_ms,
                 "fp64_pipe_slot_frac": FP64_INST_PER_XFACE_POINT * xpoints / (dom_ms / 1000.0) / FP64_SLOTS_PER_S,
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe)"}
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe)",
+                # the FP64 pipe as measured: fused multiply-add chains on every SM, outside the timing
+                "fp64_probe": {"tflops": fp64_tf, "dfma_per_clk_per_sm": fp64_per_clk, "warps_per_sm": 8,
+                               "frac_of_probe": ach / fp64_tf,
+                               "fp64_inst_per_clk_per_sm": inst_per_clk,
+                               "issue_frac_of_probe": inst_per_clk / fp64_per_clk}}
     hbm_gbs = cells * BYTES_PER_CELL_UPDATE / (sec / (world * args.steps)) / 1e9 / world
     line = {
         "metric": "2D Euler cell-updates/s", "value": value, "unit": "cell-updates/s",
@@ -530,6 +540,22 @@ def bench_euler1d(args):
                       "dtype": "f64", "data": "synthetic"}), flush=True)
 
 
+def bench_fp64_probe(args):
+    """Opt-in suite (--suite fp64-probe): the FP64 pipe's rate for fused multiply-add, multiply and
+    add chains at 4..32 warps per SM (one CTA per SM), in operations per SM clock and TFLOP/s."""
+    import torch
+
+    from paper_2304_09724_gb300 import shweno as S
+
+    torch.cuda.set_device(0)
+    rows = []
+    for op, name in ((S.FP64_FMA, "dfma"), (S.FP64_MUL, "dmul"), (S.FP64_ADD, "dadd")):
+        for w in (4, 8, 16, 32):
+            tf, per_clk = S.shweno_fp64_probe(op, w, 1 << 14)
+            rows.append({"op": name, "warps_per_sm": w, "ops_per_clk_per_sm": per_clk, "tflops": tf})
+    print(json.dumps({"suite": "fp64-probe", "chains_per_thread": 4, "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -541,7 +567,7 @@ def main():
     ap.add_argument("--ref-window", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--suite", default="main", choices=["main", "batched", "learned-run", "euler1d"])
+    ap.add_argument("--suite", default="main", choices=["main", "batched", "learned-run", "euler1d", "fp64-probe"])
     ap.add_argument("--n1d", type=int, default=4194304, help="euler1d: cells of the 1D problem")
     ap.add_argument("--dmr-nx", type=int, default=1024, help="learned-run: DMR mesh is N x N/4")
     ap.add_argument("--c5-problems", type=int, default=64)
@@ -550,6 +576,8 @@ def main():
         bench_reference(args)
     elif args.suite == "euler1d":
         bench_euler1d(args)
+    elif args.suite == "fp64-probe":
+        bench_fp64_probe(args)
     elif args.suite == "learned-run":
         bench_learned_run(args)
     elif args.suite == "batched":

@@ -47,6 +47,7 @@ EXPORTS = ["shweno_create", "shweno_set_state", "shweno_get_state", "shweno_step
            "shweno_advance", "shweno_sync", "shweno_set_timing", "shweno_get_timing",
            "shweno_kernel_name", "shweno_cfl_dt", "shweno_get_time", "shweno_set_flags",
            "shweno_destroy", "shweno_last_error", "shweno_set_allocator", "shweno_step1d_noalloc",
+           "shweno_fp64_probe",
            "shweno_flag_features", "shweno_weight_deviation", "shweno_mlp_forward", "shweno_mlp_grad",
            "shweno_mlp_adam", "shweno_set_flag_net", "shweno_get_flags", "shweno_batch_create",
            "shweno_batch_run", "shweno_batch_autotune", "shweno_batch_set", "shweno_batch_destroy",
@@ -88,6 +89,7 @@ def lib():
                                         ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_double * 4), ctypes.c_int32, vp, vp,
                                         ctypes.c_double, ctypes.c_double, vp]
+    L.shweno_fp64_probe.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, vp, dp, dp]
     L.shweno_flag_features.argtypes = [vp, vp]
     L.shweno_weight_deviation.argtypes = [vp, vp]
     L.shweno_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
@@ -210,6 +212,18 @@ def shweno_step1d_noalloc(eq, nx, x0, x1, gamma, bc, inflow, flag_mode, state_in
     infl = ((ctypes.c_double * 4) * 2)(*[(ctypes.c_double * 4)(*inflow[s]) for s in range(2)]) if inflow else None
     return lib().shweno_step1d_noalloc(eq, nx, x0, x1, gamma, kinds, infl, flag_mode, _ptr(state_in)[0],
                                        _ptr(state_out)[0], t, dt, stream or None)
+
+
+FP64_FMA, FP64_MUL, FP64_ADD = 0, 1, 2
+
+
+def shweno_fp64_probe(op=FP64_FMA, warps_per_sm=8, iters=1 << 16, stream=0):
+    """Measured FP64 rate of the current device (see include/shweno.h): returns
+    (TFLOP/s with a fused multiply-add counted 2, operations per SM clock per SM)."""
+    tf, per_clk = ctypes.c_double(), ctypes.c_double()
+    _check(lib().shweno_fp64_probe(op, warps_per_sm, iters, stream or None, ctypes.byref(tf),
+                                   ctypes.byref(per_clk)))
+    return tf.value, per_clk.value
 
 
 def shweno_flag_features(h, out):

@@ -64,6 +64,13 @@ def test_invalid_arguments_rejected_before_device_use(built):
         s = L.shweno_create(ctypes.byref(g), gamma, ctypes.byref(S.make_bc(bc)),
                             ctypes.byref(opts) if opts is not None else None, None, ctypes.byref(h))
         assert s == S.E_INVALID, (bc, gamma)
+    # FP64 probe: operation, warps per SM, iteration count and output pointer checked before any launch
+    tf = ctypes.c_double()
+    assert L.shweno_fp64_probe(3, 4, 100, None, ctypes.byref(tf), None) == S.E_INVALID
+    assert L.shweno_fp64_probe(0, 0, 100, None, ctypes.byref(tf), None) == S.E_INVALID
+    assert L.shweno_fp64_probe(0, 33, 100, None, ctypes.byref(tf), None) == S.E_INVALID
+    assert L.shweno_fp64_probe(0, 4, 0, None, ctypes.byref(tf), None) == S.E_INVALID
+    assert L.shweno_fp64_probe(0, 4, 100, None, None, None) == S.E_INVALID
     # null handle
     assert L.shweno_step(None, 0.1) == S.E_INVALID
     assert L.shweno_destroy(None) == S.OK
