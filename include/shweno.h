@@ -232,7 +232,8 @@ typedef struct shweno_batch shweno_batch;
 /* Groups n handles.  cuda_stream: stream of the batch's work (NULL: its own).
  * Errors: INVALID (null or bad handle; a 2D handle created with charwise = 1 or any handle
  * created with quintic = 1, whose items the persistent kernel does not carry), STATE (a
- * per-cell-flag handle without flags or flag network). */
+ * per-cell-flag handle without flags or flag network), NOMEM (device memory for the queue and
+ * the problem table), CUDA (stream creation or set-up upload failed). */
 shweno_status shweno_batch_create(shweno_handle* const* hs, int n, void* cuda_stream,
                                   shweno_batch** out);
 

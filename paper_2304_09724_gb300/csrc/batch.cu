@@ -458,7 +458,15 @@ shweno_status shweno_batch_create(shweno_handle* const* hs, int n, void* cuda_st
   for (int p = 0; p < n; ++p) b->has2d |= b->views[p].P.dim == 2;
   if (!b->has2d) b->ctas_per_sm = 4;
   if (cuda_stream) b->stream = (cudaStream_t)cuda_stream;
-  else { cudaStreamCreate(&b->stream); b->own_stream = true; }
+  else {
+    if (cudaStreamCreate(&b->stream) != cudaSuccess) {
+      cudaGetLastError();
+      b->stream = nullptr;
+      delete b;
+      return SHWENO_E_CUDA;
+    }
+    b->own_stream = true;
+  }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -495,9 +503,13 @@ shweno_status shweno_batch_create(shweno_handle* const* hs, int n, void* cuda_st
     shweno_batch_destroy(b);
     return SHWENO_E_NOMEM;
   }
-  cudaMemcpy(b->chunk0, ch.data(), n * sizeof(int), cudaMemcpyHostToDevice);
-  cudaFuncSetAttribute(batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem);
-  cudaFuncSetAttribute(batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem1D);
+  if (cudaMemcpy(b->chunk0, ch.data(), n * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaFuncSetAttribute(batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem1D) != cudaSuccess) {
+    cudaGetLastError();
+    shweno_batch_destroy(b);
+    return SHWENO_E_CUDA;
+  }
   *out = b;
   return SHWENO_OK;
 }
@@ -623,7 +635,6 @@ shweno_status shweno_batch_autotune(shweno_batch* b, const double* t_final, doub
   // backups of the states and control blocks
   std::vector<double*> bk(n, nullptr);
   std::vector<Ctl> cbk(n);
-  size_t total = 0;
   for (int p = 0; p < n; ++p) {
     const auto& P = b->views[p].P;
     const size_t d = (size_t)(P.dim == 2 ? 4 : 2) * P.ncomp * P.nx * P.ny;
@@ -635,7 +646,6 @@ shweno_status shweno_batch_autotune(shweno_batch* b, const double* t_final, doub
     cudaMemcpyAsync(bk[p], b->views[p].buf[0], d * sizeof(double), cudaMemcpyDeviceToDevice, b->stream);
     cudaMemcpyAsync(bk[p] + d, b->views[p].buf[1], d * sizeof(double), cudaMemcpyDeviceToDevice, b->stream);
     cudaMemcpyAsync(&cbk[p], b->views[p].ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream);
-    total += d;
   }
   cudaStreamSynchronize(b->stream);
   auto restore = [&]() {
@@ -660,7 +670,7 @@ shweno_status shweno_batch_autotune(shweno_batch* b, const double* t_final, doub
   int bt = b->tile1d, bo = b->ctas_per_sm;
   b->tuned.clear();
   shweno_status st = SHWENO_OK;
-  for (int t : tiles)
+  for (int t : tiles) {
     for (int o : occ) {
       b->tile1d = t;
       b->ctas_per_sm = o;
@@ -676,6 +686,8 @@ shweno_status shweno_batch_autotune(shweno_batch* b, const double* t_final, doub
       if (st != SHWENO_OK) break;
       if (ms < best) { best = ms; bt = t; bo = o; }
     }
+    if (st != SHWENO_OK) break;  // a failed trial ends the search; the states are restored
+  }
   b->tile1d = bt;
   b->ctas_per_sm = bo;
   b->grid = sms * bo;
@@ -683,7 +695,6 @@ shweno_status shweno_batch_autotune(shweno_batch* b, const double* t_final, doub
   for (double* q : bk) cudaFree(q);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  (void)total;
   if (tile1d_out) *tile1d_out = bt;
   if (ctas_per_sm_out) *ctas_per_sm_out = bo;
   return st;
