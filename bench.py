@@ -542,14 +542,16 @@ def bench_euler1d(args):
 
 def bench_fp64_probe(args):
     """Opt-in suite (--suite fp64-probe): the FP64 pipe's rate for fused multiply-add, multiply and
-    add chains at 4..32 warps per SM (one CTA per SM), in operations per SM clock and TFLOP/s."""
+    add chains, and for the three interleaved, at 4..32 warps per SM (one CTA per SM), in
+    operations per SM clock and TFLOP/s."""
     import torch
 
     from paper_2304_09724_gb300 import shweno as S
 
     torch.cuda.set_device(0)
     rows = []
-    for op, name in ((S.FP64_FMA, "dfma"), (S.FP64_MUL, "dmul"), (S.FP64_ADD, "dadd")):
+    for op, name in ((S.FP64_FMA, "dfma"), (S.FP64_MUL, "dmul"), (S.FP64_ADD, "dadd"),
+                     (S.FP64_MIX, "dfma,dfma,dmul,dadd")):
         for w in (4, 8, 16, 32):
             tf, per_clk = S.shweno_fp64_probe(op, w, 1 << 14)
             rows.append({"op": name, "warps_per_sm": w, "ops_per_clk_per_sm": per_clk, "tflops": tf})

@@ -285,10 +285,11 @@ shweno_status shweno_step1d_noalloc(int32_t eq, int64_t nx, double x0, double x1
 /* FP64 throughput probe (not part of the scheme): the roofline denominator of the step kernels,
  * which are bound by the FP64 pipe.  Launches one CTA of warps_per_sm (1..32) warps on every SM
  * of the current device, on cuda_stream; each thread runs four independent chains of one FP64
- * operation, op = 0 fused multiply-add, 1 multiply, 2 add, for iters (1..2^24) iterations.  Waits
- * for the launch and writes the rate in TFLOP/s (a fused multiply-add counts 2) to *tflops_out
- * and, if ops_per_clk_per_sm_out is not NULL, the operations per SM clock per SM (from the SM
- * cycle counter of one CTA).  Errors: INVALID (out of range, NULL tflops_out), CUDA. */
+ * operation, op = 0 fused multiply-add, 1 multiply, 2 add, or 3 the three interleaved (two
+ * fused chains, one product, one sum), for iters (1..2^24) iterations.  Waits for the launch and
+ * writes the rate in TFLOP/s (a fused multiply-add counts 2) to *tflops_out and, if
+ * ops_per_clk_per_sm_out is not NULL, the operations per SM clock per SM (from the SM cycle
+ * counter of one CTA).  Errors: INVALID (out of range, NULL tflops_out), CUDA. */
 shweno_status shweno_fp64_probe(int32_t op, int32_t warps_per_sm, int64_t iters, void* cuda_stream,
                                 double* tflops_out, double* ops_per_clk_per_sm_out);
 

@@ -3,8 +3,9 @@
 // The scheme runs in FP64 and its face kernels are bound by the FP64 pipe, whose rate the GPU's
 // data sheet states only loosely for this part.  The probe measures it: every thread runs four
 // independent chains of one FP64 operation -- fused multiply-add x <- x * b + c, multiply
-// x <- x * b or add x <- x + c -- for `iters` iterations (b and c are kernel arguments, so
-// nothing folds), one CTA of warps_per_sm warps per SM.  Thread 0 of CTA 0 reads the SM cycle
+// x <- x * b or add x <- x + c -- or of the three interleaved (two fused chains, one product,
+// one sum), for `iters` iterations (b and c are kernel arguments, so nothing folds), one CTA of
+// warps_per_sm warps per SM.  Thread 0 of CTA 0 reads the SM cycle
 // counter around its loop, so the call also returns the rate per SM clock, which does not depend
 // on the clock the GPU ran at.
 #include <cuda_runtime.h>
@@ -20,18 +21,27 @@ constexpr int kChains = 4;
 __device__ double g_probe_sink;
 __device__ long long g_probe_cycles;
 
-template <int OP>  // 0: fma, 1: mul, 2: add
+template <int OP>  // 0: fma, 1: mul, 2: add, 3: fma, fma, mul, add
 __global__ void fp64_probe_kernel(int64_t iters, double b, double c, double sentinel) {
   double x[kChains];
 #pragma unroll
   for (int k = 0; k < kChains; ++k) x[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+  const double ca = c * 0x1p-20;  // the sum chains' increment
   const long long c0 = clock64();
   for (int64_t i = 0; i < iters; ++i) {
+    if constexpr (OP == 3) {
+      static_assert(kChains == 4, "the mixed stream interleaves four chains");
+      x[0] = fma(x[0], b, c);
+      x[1] = fma(x[1], b, c);
+      x[2] = x[2] * b;
+      x[3] = x[3] + ca;
+    } else {
 #pragma unroll
-    for (int k = 0; k < kChains; ++k) {
-      if constexpr (OP == 0) x[k] = fma(x[k], b, c);
-      else if constexpr (OP == 1) x[k] = x[k] * b;
-      else x[k] = x[k] + c;
+      for (int k = 0; k < kChains; ++k) {
+        if constexpr (OP == 0) x[k] = fma(x[k], b, c);
+        else if constexpr (OP == 1) x[k] = x[k] * b;
+        else x[k] = x[k] + ca;
+      }
     }
   }
   double s = 0.0;
@@ -46,7 +56,7 @@ __global__ void fp64_probe_kernel(int64_t iters, double b, double c, double sent
 extern "C" shweno_status shweno_fp64_probe(int32_t op, int32_t warps_per_sm, int64_t iters,
                                            void* cuda_stream, double* tflops_out,
                                            double* ops_per_clk_per_sm_out) {
-  if (op < 0 || op > 2 || warps_per_sm < 1 || warps_per_sm > 32 || iters < 1 ||
+  if (op < 0 || op > 3 || warps_per_sm < 1 || warps_per_sm > 32 || iters < 1 ||
       iters > (int64_t(1) << 24) || !tflops_out)
     return SHWENO_E_INVALID;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -57,11 +67,12 @@ extern "C" shweno_status shweno_fp64_probe(int32_t op, int32_t warps_per_sm, int
   const int threads = 32 * warps_per_sm;
   // |x| stays near 1: with b = 1 - 2^-20 and c = 2^-20 the fused chain has the fixed point 1; the
   // product chain decays by 2^-20 and the sum chain grows by 2^-40 per iteration
-  const double b = 1.0 - 0x1p-20, c = op == 0 ? 0x1p-20 : 0x1p-40;
+  const double b = 1.0 - 0x1p-20, c = 0x1p-20;
   auto launch = [&](int64_t n) {
     if (op == 0) fp64_probe_kernel<0><<<sms, threads, 0, st>>>(n, b, c, -1.0);
     else if (op == 1) fp64_probe_kernel<1><<<sms, threads, 0, st>>>(n, b, c, -1.0);
-    else fp64_probe_kernel<2><<<sms, threads, 0, st>>>(n, b, c, -1.0);
+    else if (op == 2) fp64_probe_kernel<2><<<sms, threads, 0, st>>>(n, b, c, -1.0);
+    else fp64_probe_kernel<3><<<sms, threads, 0, st>>>(n, b, c, -1.0);
   };
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return SHWENO_E_CUDA;
@@ -82,7 +93,8 @@ extern "C" shweno_status shweno_fp64_probe(int32_t op, int32_t warps_per_sm, int
   cudaEventDestroy(e1);
   if (err != cudaSuccess || ms <= 0.0f) return SHWENO_E_CUDA;
   const double ops = (double)sms * threads * kChains * (double)iters;
-  *tflops_out = (op == 0 ? 2.0 : 1.0) * ops / (ms * 1e-3) / 1e12;
+  const double flops_per_op = op == 0 ? 2.0 : (op == 3 ? 1.5 : 1.0);
+  *tflops_out = flops_per_op * ops / (ms * 1e-3) / 1e12;
   if (ops_per_clk_per_sm_out)
     *ops_per_clk_per_sm_out = cycles > 0 ? (double)threads * kChains * (double)iters / (double)cycles : 0.0;
   return SHWENO_OK;

@@ -214,7 +214,7 @@ def shweno_step1d_noalloc(eq, nx, x0, x1, gamma, bc, inflow, flag_mode, state_in
                                        _ptr(state_out)[0], t, dt, stream or None)
 
 
-FP64_FMA, FP64_MUL, FP64_ADD = 0, 1, 2
+FP64_FMA, FP64_MUL, FP64_ADD, FP64_MIX = 0, 1, 2, 3
 
 
 def shweno_fp64_probe(op=FP64_FMA, warps_per_sm=8, iters=1 << 16, stream=0):

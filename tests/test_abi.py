@@ -66,7 +66,8 @@ def test_invalid_arguments_rejected_before_device_use(built):
         assert s == S.E_INVALID, (bc, gamma)
     # FP64 probe: operation, warps per SM, iteration count and output pointer checked before any launch
     tf = ctypes.c_double()
-    assert L.shweno_fp64_probe(3, 4, 100, None, ctypes.byref(tf), None) == S.E_INVALID
+    assert L.shweno_fp64_probe(4, 4, 100, None, ctypes.byref(tf), None) == S.E_INVALID
+    assert L.shweno_fp64_probe(-1, 4, 100, None, ctypes.byref(tf), None) == S.E_INVALID
     assert L.shweno_fp64_probe(0, 0, 100, None, ctypes.byref(tf), None) == S.E_INVALID
     assert L.shweno_fp64_probe(0, 33, 100, None, ctypes.byref(tf), None) == S.E_INVALID
     assert L.shweno_fp64_probe(0, 4, 0, None, ctypes.byref(tf), None) == S.E_INVALID
