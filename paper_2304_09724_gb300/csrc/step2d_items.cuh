@@ -23,15 +23,16 @@ struct MixTable {
 constexpr size_t kEvBytes = sizeof(double) * 8 * 5 * SPAN;
 constexpr size_t kFaceSmem = kEvBytes + sizeof(MixTable);
 
-// Weights of the cells in columns 1..SEG+1 (the cells whose faces the CTA owns).  nl(col)
-// returns whether the cell of column col uses the nonlinear weights.
+// Weights of the cells in columns 1..ncols (the cells next to the faces the CTA owns: ncols =
+// faces + 1, SEG + 1 for a full segment).  nl(col) returns whether the cell of column col uses the
+// nonlinear weights.
 // MIX = false (characteristic-wise reconstruction, whose weights belong to each face point):
 // only the flags are recorded.
 template <int NC, bool MIX, bool Q, typename FlagOf>
 __device__ __forceinline__ void cell_mixes(const Params& P, const double (*ev)[5][SPAN],
-                                           MixTable& mt, FlagOf nl) {
-  for (int it = threadIdx.x; it < (MIX ? NC : 1) * (SEG + 1); it += SEG) {
-    const int q = it / (SEG + 1), c = 1 + it % (SEG + 1);
+                                           MixTable& mt, int ncols, FlagOf nl) {
+  for (int it = threadIdx.x; it < (MIX ? NC : 1) * ncols; it += SEG) {
+    const int q = it / ncols, c = 1 + it % ncols;
     const int nonlinear = nl(c);
     if (q == 0) mt.lin[c] = !nonlinear;
     if (!MIX || !nonlinear) continue;
@@ -362,8 +363,10 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv, 
   MixTable& mt = *reinterpret_cast<MixTable*>(smem_raw + kEvBytes);
   const int NX4 = P.nx + 4, NY2 = P.ny + 2;
   using namespace shweno_tables;
-  for (int it = threadIdx.x; it < 2 * NC * SPAN; it += SEG) {
-    const int col = it % SPAN, rq = it / SPAN;
+  // faces x_{f0-1/2} .. x_{f0+nf-3/2} exist; their stencils span columns 0 .. nf + 2
+  const int nf = min(SEG, P.nx + 1 - f0), ncol = nf + 3;
+  for (int it = threadIdx.x; it < 2 * NC * ncol; it += SEG) {
+    const int col = it % ncol, rq = it / ncol;
     const int tcol = f0 + col;
     double e[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (tcol >= NX4) {
@@ -405,7 +408,7 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv, 
   }
   __syncthreads();
   // cell column c holds cell i = f0 + c - 2; a corner row uses the rows below and above
-  cell_mixes<NC, !CHAR, Q>(P, ev, mt, [&](int c) {
+  cell_mixes<NC, !CHAR, Q>(P, ev, mt, nf + 1, [&](int c) {
     const int i = f0 + c - 2;
     return slice < 3 ? cell_flag(P, flag, i, row)
                      : (cell_flag(P, flag, i, row - 1) | cell_flag(P, flag, i, row));
@@ -453,8 +456,10 @@ __device__ __forceinline__ void yface_item(const Params& P, const StepView& sv, 
   MixTable& mt = *reinterpret_cast<MixTable*>(smem_raw + kEvBytes);
   const int NY4 = P.ny + 4;
   using namespace shweno_tables;
-  for (int it = threadIdx.x; it < 2 * NC * SPAN; it += SEG) {
-    const int r = it % SPAN, rq = it / SPAN;
+  // faces y_{f0-1/2} .. y_{f0+nf-3/2} exist; their stencils span rows 0 .. nf + 2
+  const int nf = min(SEG, P.ny + 1 - f0), nrow = nf + 3;
+  for (int it = threadIdx.x; it < 2 * NC * nrow; it += SEG) {
+    const int r = it % nrow, rq = it / nrow;
     const int trow = f0 + r;
     double e[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (trow < NY4) {
@@ -472,7 +477,7 @@ __device__ __forceinline__ void yface_item(const Params& P, const StepView& sv, 
     for (int k = 0; k < 5; ++k) ev[rq][k][r] = e[k];
   }
   __syncthreads();
-  cell_mixes<NC, !CHAR, Q>(P, ev, mt, [&](int c) { return cell_flag(P, flag, col, f0 + c - 2); });
+  cell_mixes<NC, !CHAR, Q>(P, ev, mt, nf + 1, [&](int c) { return cell_flag(P, flag, col, f0 + c - 2); });
   __syncthreads();
   const int fj = f0 + threadIdx.x;  // face y_{fj-1/2}
   if (fj > P.ny) return;
