@@ -62,8 +62,8 @@ struct BatchCtl {
   int timeout;              // a wait ran out
 };
 
-constexpr size_t kBatchSmem = kFaceSmem > sizeof(double) * 16 * (TYB + 2) * (TX + 2) ?
-                              kFaceSmem : sizeof(double) * 16 * (TYB + 2) * (TX + 2);
+constexpr size_t kBatchSmem = kFaceSmemFlags > sizeof(double) * 16 * (TYB + 2) * (TX + 2) ?
+                              kFaceSmemFlags : sizeof(double) * 16 * (TYB + 2) * (TX + 2);
 constexpr size_t kBatchSmem1D = sizeof(double) * 2 * 3 * (1024 + 1);  // F-hat and W(t+dt) of a tile
 static_assert(kBatchSmem1D <= kBatchSmem, "1D tiles fit the 2D batch's shared memory");
 

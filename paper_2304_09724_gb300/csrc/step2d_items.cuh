@@ -20,17 +20,28 @@ struct MixTable {
   int lin[SPAN];                               // 1: the cell uses the linear weights (p = p1)
 };
 
+// The small-stencil terms of the mixed polynomial at the cell's ends, per (comp, cell column):
+// at the right end e0 gains P0 d(W0) - hB d(W-) + hC d(W+), at the left end
+// M0 d(W0) + hB d(W-) - hC d(W+), and at both ends e1 gains BmC d(W0) - B d(W-) + C d(W+)
+// (P0 = 1.5 B + 0.5 C, M0 = 0.5 B + 1.5 C, hB = B / 2, hC = C / 2, BmC = B - C).  The flagged
+// kernels, which reload the weights from shared memory for every tangential order, read these
+// instead of forming them again for each order.
+struct MixExtra {
+  double P0[4][SPAN], M0[4][SPAN], hB[4][SPAN], hC[4][SPAN], BmC[4][SPAN];
+};
+
 constexpr size_t kEvBytes = sizeof(double) * 8 * 5 * SPAN;
 constexpr size_t kFaceSmem = kEvBytes + sizeof(MixTable);
+constexpr size_t kFaceSmemFlags = kFaceSmem + sizeof(MixExtra);  // flagged kernels
 
 // Weights of the cells in columns 1..ncols (the cells next to the faces the CTA owns: ncols =
 // faces + 1, SEG + 1 for a full segment).  nl(col) returns whether the cell of column col uses the
 // nonlinear weights.
 // MIX = false (characteristic-wise reconstruction, whose weights belong to each face point):
 // only the flags are recorded.
-template <int NC, bool MIX, bool Q, typename FlagOf>
+template <int NC, bool MIX, bool Q, bool EXTRA, typename FlagOf>
 __device__ __forceinline__ void cell_mixes(const Params& P, const double (*ev)[5][SPAN],
-                                           MixTable& mt, int ncols, FlagOf nl) {
+                                           MixTable& mt, MixExtra* mx, int ncols, FlagOf nl) {
   for (int it = threadIdx.x; it < (MIX ? NC : 1) * ncols; it += SEG) {
     const int q = it / ncols, c = 1 + it % ncols;
     const int nonlinear = nl(c);
@@ -43,6 +54,13 @@ __device__ __forceinline__ void cell_mixes(const Params& P, const double (*ev)[5
     mt.A[q][c] = m.A;
     mt.B[q][c] = m.B;
     mt.C[q][c] = m.C;
+    if constexpr (EXTRA) {
+      mx->P0[q][c] = 1.5 * m.B + 0.5 * m.C;
+      mx->M0[q][c] = 0.5 * m.B + 1.5 * m.C;
+      mx->hB[q][c] = 0.5 * m.B;
+      mx->hC[q][c] = 0.5 * m.C;
+      mx->BmC[q][c] = m.B - m.C;
+    }
   }
 }
 
@@ -67,6 +85,37 @@ __device__ __forceinline__ void side_out_d(const double* d, int k, double A, dou
   if (PLUS) e[0] += (1.5 * B + 0.5 * C) * d[1] - 0.5 * B * d[0] + 0.5 * C * d[2];
   else e[0] += (0.5 * B + 1.5 * C) * d[1] + 0.5 * B * d[0] - 0.5 * C * d[2];
   if (k <= 3) e[1] += (B - C) * d[1] - B * d[0] + C * d[2];
+}
+// side_out_d with the small-stencil coefficients precomputed (MixExtra): e0 gains
+// x1 d(W0) + x0 d(W-) + x2 d(W+) and e1 gains y1 d(W0) + y0 d(W-) + y2 d(W+).
+template <bool PLUS, bool Q = false>
+__device__ __forceinline__ void side_out_pre(const double* d, int k, double A, double x1, double x0,
+                                             double x2, double y1, double y0, double y2, bool lin,
+                                             double e[5]) {
+  using namespace shweno_tables;
+  if (lin) {
+#pragma unroll
+    for (int p = 0; p + k <= 4; ++p) e[p] = Q ? qend_dot<PLUS>(p, d) : end_dot<PLUS>(p, d);
+    return;
+  }
+#pragma unroll
+  for (int p = 0; p + k <= 4; ++p) e[p] = A * (Q ? qend_dot<PLUS>(p, d) : end_dot<PLUS>(p, d));
+  e[0] += x1 * d[1] + x0 * d[0] + x2 * d[2];
+  if (k <= 3) e[1] += y1 * d[1] + y0 * d[0] + y2 * d[2];
+}
+template <int NC, bool PLUS, bool Q = false>
+__device__ __forceinline__ void side_out_x(const double (*ev)[5][SPAN], int c0, int q, int k, double A,
+                                           double x1, double x0, double x2, double y1, double y0,
+                                           double y2, bool lin, double e[5]) {
+  if constexpr (Q) {
+    const double d[6] = {ev[q][k][c0], ev[q][k][c0 + 1], ev[q][k][c0 + 2], ev[NC + q][k][c0],
+                         ev[NC + q][k][c0 + 1], ev[NC + q][k][c0 + 2]};
+    side_out_pre<PLUS, true>(d, k, A, x1, x0, x2, y1, y0, y2, lin, e);
+  } else {
+    const double d[5] = {ev[q][k][c0], ev[q][k][c0 + 1], ev[q][k][c0 + 2], ev[NC + q][k][c0],
+                         ev[NC + q][k][c0 + 2]};
+    side_out_pre<PLUS>(d, k, A, x1, x0, x2, y1, y0, y2, lin, e);
+  }
 }
 template <int NC, bool PLUS, bool Q = false>
 __device__ __forceinline__ void side_out(const double (*ev)[5][SPAN], int c0, int q, int k, double A,
@@ -144,8 +193,8 @@ __device__ __forceinline__ void char_sides(const CharBasis<NC>& Bs, const double
 // the point), with its own weights per field and side (the MixTable then holds only the flags).
 template <int NC, bool FLAGS, bool CHAR = false, bool Q = false>
 __device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5][SPAN],
-                                           const MixTable& mt, int c0, int dir, double tc[NC][5],
-                                           const double* Wref = nullptr) {
+                                           const MixTable& mt, const MixExtra* mx, int c0, int dir,
+                                           double tc[NC][5], const double* Wref = nullptr) {
   static_assert(!CHAR || NC == 4, "characteristic fields are for the Euler system");
   const double g = P.gamma;
   double a[NC][25];
@@ -205,19 +254,32 @@ __device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5
         char_sides<NC, Q>(Bs, xw, xv, k, AL, BL, CL, linL, AR, BR, CR, linR, dl, dr);
       } else {
         if constexpr (FLAGS) {
-          // the flagged instantiation reloads the weights from shared memory for every order
-          // (measured: 3 % faster for it; the plain one is 3 % faster keeping them in registers)
+          // the flagged instantiation reloads the weights and the small-stencil coefficients
+          // from shared memory for every order (measured: faster for it; the plain one is 3 %
+          // faster keeping the weights in registers)
           const volatile double* vA = &mt.A[0][0];
           const volatile double* vB = &mt.B[0][0];
           const volatile double* vC = &mt.C[0][0];
+          const volatile double* vP0 = &mx->P0[0][0];
+          const volatile double* vM0 = &mx->M0[0][0];
+          const volatile double* vhB = &mx->hB[0][0];
+          const volatile double* vhC = &mx->hC[0][0];
+          const volatile double* vBmC = &mx->BmC[0][0];
 #pragma unroll
           for (int q = 0; q < NC; ++q) {
-            const double aL = linL ? 1.0 : vA[q * SPAN + c0 + 1], bL = linL ? 0.0 : vB[q * SPAN + c0 + 1];
-            const double cL = linL ? 0.0 : vC[q * SPAN + c0 + 1];
-            const double aR = linR ? 1.0 : vA[q * SPAN + c0 + 2], bR = linR ? 0.0 : vB[q * SPAN + c0 + 2];
-            const double cR = linR ? 0.0 : vC[q * SPAN + c0 + 2];
-            side_out<NC, true, Q>(ev, c0, q, k, aL, bL, cL, linL, dl[q]);
-            side_out<NC, false, Q>(ev, c0 + 1, q, k, aR, bR, cR, linR, dr[q]);
+            const int l = q * SPAN + c0 + 1, r = l + 1;
+            if (linL) {
+              side_out_x<NC, true, Q>(ev, c0, q, k, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, true, dl[q]);
+            } else {
+              side_out_x<NC, true, Q>(ev, c0, q, k, vA[l], vP0[l], -vhB[l], vhC[l], vBmC[l], -vB[l],
+                                      vC[l], false, dl[q]);
+            }
+            if (linR) {
+              side_out_x<NC, false, Q>(ev, c0 + 1, q, k, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, true, dr[q]);
+            } else {
+              side_out_x<NC, false, Q>(ev, c0 + 1, q, k, vA[r], vM0[r], vhB[r], -vhC[r], vBmC[r], -vB[r],
+                                       vC[r], false, dr[q]);
+            }
           }
         } else {
 #pragma unroll
@@ -352,7 +414,8 @@ __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv,
 }
 
 // x-face Gauss points (slice 0..2, cell row `row`) or corner points (slice 3, corner row `row`
-// at y_{row-1/2}) of faces x_{f0-1/2} .. x_{f0+SEG-3/2}; SEG threads, smem_raw of kFaceSmem bytes.
+// at y_{row-1/2}) of faces x_{f0-1/2} .. x_{f0+SEG-3/2}; SEG threads, smem_raw of kFaceSmem bytes
+// (kFaceSmemFlags for the flagged kernels).
 template <int NC, bool FLAGS, bool CHAR = false, bool Q = false>
 __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv, const double* st,
                                            const double* __restrict__ ycoef,
@@ -408,7 +471,8 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv, 
   }
   __syncthreads();
   // cell column c holds cell i = f0 + c - 2; a corner row uses the rows below and above
-  cell_mixes<NC, !CHAR, Q>(P, ev, mt, nf + 1, [&](int c) {
+  MixExtra* mx = FLAGS && !CHAR ? reinterpret_cast<MixExtra*>(smem_raw + kFaceSmem) : nullptr;
+  cell_mixes<NC, !CHAR, Q, FLAGS && !CHAR>(P, ev, mt, mx, nf + 1, [&](int c) {
     const int i = f0 + c - 2;
     return slice < 3 ? cell_flag(P, flag, i, row)
                      : (cell_flag(P, flag, i, row - 1) | cell_flag(P, flag, i, row));
@@ -428,7 +492,7 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv, 
                           fetch(P, st, 0, q, fi - 1, row, sv.t) + fetch(P, st, 0, q, fi, row, sv.t));
     }
   }
-  face_point<NC, FLAGS, CHAR, Q>(P, ev, mt, threadIdx.x, 0, tc, Wref);
+  face_point<NC, FLAGS, CHAR, Q>(P, ev, mt, mx, threadIdx.x, 0, tc, Wref);
   const double dt = sv.dt;
   if (slice < 3) {
     double Fh[NC], We[NC];
@@ -477,7 +541,9 @@ __device__ __forceinline__ void yface_item(const Params& P, const StepView& sv, 
     for (int k = 0; k < 5; ++k) ev[rq][k][r] = e[k];
   }
   __syncthreads();
-  cell_mixes<NC, !CHAR, Q>(P, ev, mt, nf + 1, [&](int c) { return cell_flag(P, flag, col, f0 + c - 2); });
+  MixExtra* mx = FLAGS && !CHAR ? reinterpret_cast<MixExtra*>(smem_raw + kFaceSmem) : nullptr;
+  cell_mixes<NC, !CHAR, Q, FLAGS && !CHAR>(P, ev, mt, mx, nf + 1,
+                                           [&](int c) { return cell_flag(P, flag, col, f0 + c - 2); });
   __syncthreads();
   const int fj = f0 + threadIdx.x;  // face y_{fj-1/2}
   if (fj > P.ny) return;
@@ -488,7 +554,7 @@ __device__ __forceinline__ void yface_item(const Params& P, const StepView& sv, 
     for (int q = 0; q < NC; ++q)
       Wref[q] = 0.5 * (fetch(P, st, 0, q, col, fj - 1, sv.t) + fetch(P, st, 0, q, col, fj, sv.t));
   }
-  face_point<NC, FLAGS, CHAR, Q>(P, ev, mt, threadIdx.x, 1, tc, Wref);
+  face_point<NC, FLAGS, CHAR, Q>(P, ev, mt, mx, threadIdx.x, 1, tc, Wref);
   double Gh[NC], We[NC];
   lobatto<NC>(tc, sv.dt, P.gamma, 1, Gh, We);
 #pragma unroll

@@ -97,8 +97,8 @@ template <int NC, bool CHAR, bool Q>
 static void init_kernels2d_nc() {
   cudaFuncSetAttribute(xface2d_kernel<NC, false, CHAR, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
   cudaFuncSetAttribute(yface2d_kernel<NC, false, CHAR, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
-  cudaFuncSetAttribute(xface2d_kernel<NC, true, CHAR, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
-  cudaFuncSetAttribute(yface2d_kernel<NC, true, CHAR, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
+  cudaFuncSetAttribute(xface2d_kernel<NC, true, CHAR, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmemFlags);
+  cudaFuncSetAttribute(yface2d_kernel<NC, true, CHAR, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmemFlags);
 }
 
 // Attributes of every face kernel of one reading (Q = false: R1, true: R1').
@@ -118,13 +118,13 @@ static void launch_faces2d(const Params& P, Ctl* ctl, const double* s0, const do
   if (P.flag_mode == FLAG_ALL_NONLINEAR)
     xface2d_kernel<NC, false, CHAR, Q><<<xg, SEG, kFaceSmem, st>>>(P, ctl, s0, s1, S.ycoef, flag, S.FX, S.WX, S.WC);
   else
-    xface2d_kernel<NC, true, CHAR, Q><<<xg, SEG, kFaceSmem, st>>>(P, ctl, s0, s1, S.ycoef, flag, S.FX, S.WX, S.WC);
+    xface2d_kernel<NC, true, CHAR, Q><<<xg, SEG, kFaceSmemFlags, st>>>(P, ctl, s0, s1, S.ycoef, flag, S.FX, S.WX, S.WC);
   if (ev) cudaEventRecord(ev[2], st);
   dim3 yg((P.ny + 1 + SEG - 1) / SEG, P.nx, 3);
   if (P.flag_mode == FLAG_ALL_NONLINEAR)
     yface2d_kernel<NC, false, CHAR, Q><<<yg, SEG, kFaceSmem, st>>>(P, ctl, s0, s1, S.xcoef, flag, S.FY, S.WY);
   else
-    yface2d_kernel<NC, true, CHAR, Q><<<yg, SEG, kFaceSmem, st>>>(P, ctl, s0, s1, S.xcoef, flag, S.FY, S.WY);
+    yface2d_kernel<NC, true, CHAR, Q><<<yg, SEG, kFaceSmemFlags, st>>>(P, ctl, s0, s1, S.xcoef, flag, S.FY, S.WY);
 }
 
 template <int NC, bool Q>
