@@ -385,7 +385,8 @@ __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv,
         const double v0 = Q ? P.dy * tile[fd][ly][lx] : 0.0;
         double c[6], C[6];
         p1_coeffs_t<Q>(Wm, W0, Wp, vm, v0, vp, c);
-        mix_coeffs_t<Q>(shweno_mix_t<Q>(P, Wm, W0, Wp, c, nl), Wm, W0, Wp, c, C);
+        if (nl) mix_coeffs_t<Q>(shweno_mix_t<Q>(P, Wm, W0, Wp, c, 1), Wm, W0, Wp, c, C);
+        else for (int k = 0; k < 6; ++k) C[k] = c[k];  // linear weights: p = p1
         const double sc = s == 0 ? 1.0 : P.dx;  // x-pass derivative data: dx * avg(W_x)
 #pragma unroll
         for (int k = 0; k < KC; ++k)
@@ -404,7 +405,8 @@ __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv,
         const double v0 = Q ? P.dx * tile[fd][ly][lx] : 0.0;
         double c[6], C[6];
         p1_coeffs_t<Q>(Wm, W0, Wp, vm, v0, vp, c);
-        mix_coeffs_t<Q>(shweno_mix_t<Q>(P, Wm, W0, Wp, c, nl), Wm, W0, Wp, c, C);
+        if (nl) mix_coeffs_t<Q>(shweno_mix_t<Q>(P, Wm, W0, Wp, c, 1), Wm, W0, Wp, c, C);
+        else for (int k = 0; k < 6; ++k) C[k] = c[k];  // linear weights: p = p1
         const double sc = s == 0 ? 1.0 : P.dy;  // y-pass derivative data: dy * avg(W_y)
 #pragma unroll
         for (int k = 0; k < KC; ++k)
