@@ -32,9 +32,10 @@ struct Params {
   // Cauchy-Kovalevskaya scale factors (m+1)/((k+1) dx) and (n+1)/((k+1) dy), set by the host
   double ckx[5][4], cky[5][4];
   double igam[3];  // 1 / gam, set by the host
+  double idx, idy, idxy;  // 1 / dx, 1 / dy, 1 / (dx dy), set by the host
 };
 
-// Fills the derived members of Params (ckx, cky, igam) from dx, dy and gam.
+// Fills the derived members of Params (ckx, cky, igam, idx, idy, idxy) from dx, dy and gam.
 inline void finalize_params(Params& P) {
   for (int m = 0; m < 5; ++m)
     for (int k = 0; k < 4; ++k) {
@@ -42,6 +43,9 @@ inline void finalize_params(Params& P) {
       P.cky[m][k] = (m + 1) / ((k + 1) * P.dy);
     }
   for (int l = 0; l < 3; ++l) P.igam[l] = 1.0 / P.gam[l];
+  P.idx = 1.0 / P.dx;
+  P.idy = 1.0 / P.dy;
+  P.idxy = 1.0 / (P.dx * P.dy);
 }
 
 // Device-resident time-stepping control block.  One step = begin_step, the step kernels,
