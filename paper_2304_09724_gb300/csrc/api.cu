@@ -543,10 +543,12 @@ shweno_status shweno_advance(shweno_handle* h, int64_t nsteps, double cfl) {
     return SHWENO_OK;
   }
   const int G = 4;
-  shweno_status s = build_graph(h, G);
-  if (s != SHWENO_OK) return s;
   int64_t k = 0;
-  for (; k + G <= nsteps; k += G) CK(h, cudaGraphLaunch(h->graph, h->stream));
+  if (nsteps >= G) {  // fewer steps go out as plain launches: no graph to capture for them
+    shweno_status s = build_graph(h, G);
+    if (s != SHWENO_OK) return s;
+    for (; k + G <= nsteps; k += G) CK(h, cudaGraphLaunch(h->graph, h->stream));
+  }
   for (; k < nsteps; ++k) CK(h, enqueue_step(h));
   return SHWENO_OK;
 }
