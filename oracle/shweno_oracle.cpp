@@ -1152,7 +1152,7 @@ void orc_step2d_cells(const orc_problem* P, const double* W, const double* V, co
   step2d_cells(S, dt, ncells, ij, out);
 }
 
-// ----- learned troubled-cell flag (not in the paper; the task's learned layer) -----
+// ----- learned troubled-cell flag (not in the paper; the learned layer of the library) -----
 // Label source: the largest relative deviation max_l |w_l - gamma_l| / gamma_l of the nonlinear
 // weights of the 16 first-pass reconstructions anchored on cell (i, j) (y-pass on {W,Y} and
 // {V,Z}, x-pass on {W,V} and {Y,Z}, four components) in the always-nonlinear scheme.
