@@ -133,7 +133,7 @@ __device__ void do_item(const BatchProblem& B, int kind, long long idx, unsigned
           const int fo = q * (B.tile1d + 1) + k;
           Wn[q] = __ldcg(st + (size_t)q * P.nx + j) - sv.dt / P.dx * (FH[fo + 1] - FH[fo]);
           out[(size_t)q * P.nx + j] = Wn[q];
-          out[(size_t)(P.ncomp + q) * P.nx + j] = (WE[fo + 1] - WE[fo]) / P.dx;
+          out[(size_t)(P.ncomp + q) * P.nx + j] = (WE[fo + 1] - WE[fo]) * P.idx;
         }
         if (!cell_physical(P, Wn)) atomicCAS(&ctl->err, ERR_NONE, ERR_NONPHYSICAL);
         else rate = fmax(rate, cell_rate(P, Wn));

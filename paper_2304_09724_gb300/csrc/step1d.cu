@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) update1d_kernel(Params P, Ctl* __restrict
       const size_t fo = (size_t)q * (N + 1) + j;
       Wn[q] = st[(size_t)q * N + j] - dt / P.dx * (FH[fo + 1] - FH[fo]);
       out[(size_t)q * N + j] = Wn[q];
-      out[(size_t)(nc + q) * N + j] = (WE[fo + 1] - WE[fo]) / P.dx;
+      out[(size_t)(nc + q) * N + j] = (WE[fo + 1] - WE[fo]) * P.idx;  // 1 / dx from the host
     }
     if (!cell_physical(P, Wn)) atomicCAS(&ctl->err, ERR_NONE, ERR_NONPHYSICAL);
     else rate = cell_rate(P, Wn);
