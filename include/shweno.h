@@ -132,8 +132,10 @@ shweno_status shweno_run(shweno_handle* h, double t_final, double cfl, double* t
                          int64_t* nsteps_out);
 
 /* Enqueues exactly nsteps CFL steps (dt = cfl / rate, no end time) and returns without waiting.
- * A non-physical step stops the sequence on the device (the last good state stays committed);
- * the error is reported by the next shweno_sync.  Used for throughput measurement. */
+ * Groups of four steps go out as one CUDA graph (captured on first use and kept); the remaining
+ * steps, and calls for fewer than four, go out as plain launches.  A non-physical step stops the
+ * sequence on the device (the last good state stays committed); the error is reported by the next
+ * shweno_sync.  Used for throughput measurement. */
 shweno_status shweno_advance(shweno_handle* h, int64_t nsteps, double cfl);
 
 /* Waits for the handle's stream; returns NONPHYSICAL if a step since the last call failed. */
