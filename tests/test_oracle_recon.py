@@ -137,3 +137,71 @@ def test_quadrature_rules_exact():
     assert lam[0] == 0.0 and lam[-1] == 1.0  # the rule holds both ends (Remark 2)
     # degree 6 is not integrated exactly by the 3-node Gauss rule (so the rule is not larger)
     assert abs(np.dot(gw, gs ** 6) - 2 * 0.5 ** 7 / 7) > 1e-6
+
+
+# ---------------------------------------------------------------- weights evaluated by hand
+# Two data sets whose big-stencil quartic, smoothness indicators and weights are worked out in
+# exact rationals below, independently of the oracle (which solves the 5x5 system numerically and
+# integrates the squared derivatives monomial by monomial).  Reading R1 of Section 2.4 (the
+# simple-WENO form): tau = ((|b1 - b2| + |b1 - b3|)/2)^2, w~_l = gamma_l (1 + tau/(b_l + eps)),
+# w_l = w~_l / sum w~, eps = 1e-6, gamma = (0.994, 0.003, 0.003).
+HALF = sp.Rational(1, 2)
+GAM_Q = (sp.Rational(994, 1000), sp.Rational(3, 1000), sp.Rational(3, 1000))
+EPS_Q = sp.Rational(1, 10 ** 6)
+XI = sp.Symbol("xi")
+HAND_CASES = [
+    # step data: W = (0, 0, 1), v = (0, 0).
+    #   p1 = -xi^4/2 - xi^3/4 + 5 xi^2/4 + 13 xi/16 - 47/480, beta1 = 219889/1344,
+    #   p2 = 0 (beta2 = 0), p3 = xi (beta3 = 1), tau = (beta1 - 1/2)^2 since beta1 > 1
+    dict(W=(0, 0, 1), v=(0, 0),
+         p1=-XI ** 4 / 2 - XI ** 3 / 4 + sp.Rational(5, 4) * XI ** 2 + sp.Rational(13, 16) * XI
+         - sp.Rational(47, 480),
+         beta=(sp.Rational(219889, 1344), 0, 1)),
+    # averages and derivative averages of the quadratic p = xi^2/20 + 3 xi/20 + 23/240:
+    #   W = (0, 1/10, 3/10), v = (1/20, 1/4); p1 = p, beta1 = (3/20)^2 + (1/10)^2/12 + (1/10)^2
+    #   = 1/30, beta2 = (1/10)^2, beta3 = (1/5)^2, tau = ((7/300 + 2/300)/2)^2 = (3/200)^2
+    dict(W=(0, sp.Rational(1, 10), sp.Rational(3, 10)), v=(sp.Rational(1, 20), sp.Rational(1, 4)),
+         p1=XI ** 2 / 20 + sp.Rational(3, 20) * XI + sp.Rational(23, 240),
+         beta=(sp.Rational(1, 30), sp.Rational(1, 100), sp.Rational(1, 25))),
+]
+
+
+def _exact_weights(beta, tau_of=lambda b: ((abs(b[0] - b[1]) + abs(b[0] - b[2])) / 2) ** 2,
+                   shape=lambda g, t, b: g * (1 + t / (b + EPS_Q))):
+    tau = tau_of(beta)
+    wt = [shape(g, tau, b) for g, b in zip(GAM_Q, beta)]
+    s = sum(wt)
+    return [w / s for w in wt]
+
+
+@pytest.mark.parametrize("case", range(len(HAND_CASES)))
+def test_weights_hand_evaluated(case):
+    c = HAND_CASES[case]
+    xi = XI
+    p1 = c["p1"]
+    # the quartic satisfies the five conditions of reading R1 (cell averages over cells -1, 0, +1
+    # and derivative averages over cells -1, +1), which fix it uniquely
+    for l, w in zip((-1, 0, 1), c["W"]):
+        assert sp.integrate(p1, (xi, l - HALF, l + HALF)) == w
+    for l, w in zip((-1, 1), c["v"]):
+        assert p1.subs(xi, l + HALF) - p1.subs(xi, l - HALF) == w
+    # smoothness indicators: the stated closed forms equal the integrals of the squared derivatives
+    b1 = sum(sp.integrate(sp.diff(p1, xi, a) ** 2, (xi, -HALF, HALF)) for a in range(1, 5))
+    assert b1 == c["beta"][0]
+    W = c["W"]
+    assert (W[1] - W[0]) ** 2 == c["beta"][1] and (W[2] - W[1]) ** 2 == c["beta"][2]
+    Wf, vf = [float(a) for a in W], [float(a) for a in c["v"]]
+    assert O.smoothness(O.big_poly(Wf, vf)) == pytest.approx(float(b1), rel=1e-13)
+    expect = [float(w) for w in _exact_weights(c["beta"])]
+    got = O.weights(Wf, vf)
+    np.testing.assert_allclose(got, expect, rtol=1e-12, atol=1e-15)
+    # the case tells the formula apart from its plausible slips: tau left unsquared, the 1/2
+    # dropped, or the bracket squared all move some weight by far more than the tolerance
+    slips = [
+        _exact_weights(c["beta"], tau_of=lambda b: (abs(b[0] - b[1]) + abs(b[0] - b[2])) / 2),
+        _exact_weights(c["beta"], tau_of=lambda b: (abs(b[0] - b[1]) + abs(b[0] - b[2])) ** 2),
+        _exact_weights(c["beta"], shape=lambda g, t, b: g * (1 + t / (b + EPS_Q)) ** 2),
+    ]
+    for s in slips:
+        rel = max(abs(float(a) - e) / e for a, e in zip(s, expect))
+        assert rel > 1e-6
