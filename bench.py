@@ -33,9 +33,9 @@ CFL = 0.6
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP64_SLOTS_PER_S = 152 * 2 * 2.070e9  # FP64 thread instructions per second (DFMA, DMUL, DADD alike)
 # FP64 operations (DFMA counted as 2) and FP64 thread instructions (DFMA + DMUL + DADD, each one
-# pipe slot) per x-face point of xface2d, from the ncu instruction counters of the committed
-# kernel on the 2048^2 launch (profiles/fp64_pipe_vortex2048.md), and its DRAM bytes per point from
-# the 512^2 capture (profiles/xface2d_vortex512.md; traffic grows in proportion to the points).
+# pipe slot) per x-face point of xface2d, from ncu's instruction counters of the current kernel on
+# the 2048^2 launch, and its DRAM bytes per point from a capture at 512^2 (traffic grows in
+# proportion to the points).
 FLOPS_PER_XFACE_POINT = 5746.5
 FP64_INST_PER_XFACE_POINT = 3320.0
 DRAM_BYTES_PER_XFACE_POINT = 344.3

@@ -262,22 +262,26 @@ shweno_status shweno_batch_destroy(shweno_batch* b);
 const char* shweno_batch_last_error(const shweno_batch* b);
 
 /* Allocation-free single 1D step.  The paper has no counterpart: this is a convenience for
- * callers that cannot allocate device memory when they step -- code running inside an open
- * CUDA stream capture (allocation is not capturable and synchronises the device), real-time
- * loops that cannot take an allocation's latency, and frameworks that own all device memory
- * through their own pool.  It advances one 1D state by dt (Section 2 scheme, same kernels as
- * shweno_step) without any allocation: the step's scratch (per-face fluxes and states and the
- * kernels' control block) lives in one fixed __device__ array of 256 bytes + 48 (nx_max + 1)
- * bytes (about 3.1 MB) that every GPU loading this library holds until exit.
+ * callers that cannot allocate device memory when they step -- real-time loops that cannot take
+ * an allocation's latency or the device-wide synchronisation that freeing memory implies, and
+ * frameworks that own all device memory through their own pool.  It advances one 1D state by dt
+ * with the same kernels as shweno_step, without any allocation: the step's scratch (per-face
+ * fluxes and states and the kernels' control block) lives in one fixed __device__ array of
+ * 256 bytes + 48 (nx_max + 1) bytes (about 3.1 MB) that every GPU loading this library holds
+ * until exit.
  *   eq, nx (4 <= nx <= SHWENO_NOALLOC_MAX_NX), [x0, x1], gamma, bc_kind[2] (x-low, x-high;
- *   PERIODIC, OUTFLOW, REFLECTIVE or INFLOW), inflow[2][4] (may be NULL), flag_mode 0 or 1;
+ *   PERIODIC, OUTFLOW, REFLECTIVE or INFLOW; periodic on both sides or on neither),
+ *   inflow[2][4] (the conserved state of an INFLOW side; may be NULL only when no side is
+ *   INFLOW), flag_mode 0 (nonlinear weights in every cell) or 1 (linear weights in every cell);
  *   state_in / state_out: device pointers to [2][ncomp][nx] float64 (W then V), not
  *   overlapping; t: time of state_in; dt > 0; cuda_stream: the stream the work is ordered on.
- * The call waits for the step and returns NONPHYSICAL if the new state has rho <= 0, p <= 0 or
- * a NaN (state_out then holds that state; state_in is untouched).  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress, with that device current) and
- * caches it, so it should come before any stream capture.  All calls share the one array: calls
- * that overlap on the GPU race.  Sizes beyond the maximum return INVALID. */
+ * The call waits for the step (it synchronises cuda_stream) and returns NONPHYSICAL if the new
+ * state has rho <= 0, p <= 0 or a NaN (state_out then holds that state; state_in is untouched).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current) and caches it for the process, so it should come before any stream
+ * capture, and no call may follow a cudaDeviceReset of that device.  All calls share the one
+ * array: calls that overlap on the GPU race.  Sizes beyond the maximum and any other bad
+ * argument return INVALID. */
 #define SHWENO_NOALLOC_MAX_NX 65536
 shweno_status shweno_step1d_noalloc(int32_t eq, int64_t nx, double x0, double x1, double gamma,
                                     const int32_t bc_kind[2], const double inflow[2][4],

@@ -344,7 +344,12 @@ shweno_status shweno_create(const shweno_grid* grid, double gamma, const shweno_
   if (!h->scratch) return bail(SHWENO_E_NOMEM, "device allocation of the step scratch failed");
   if (dim == 2) {
     h->S = shweno::carve_scratch2d(P, h->scratch);
-    shweno::init_kernels2d();
+    const cudaError_t ea = shweno::init_kernels2d();
+    if (ea != cudaSuccess) {
+      cudaGetLastError();
+      return bail(SHWENO_E_CUDA, std::string("setting the face kernels' shared memory limit failed: ") +
+                                     cudaGetErrorString(ea));
+    }
   }
   else { h->FH = h->scratch; h->WE = h->scratch + (size_t)P.ncomp * (P.nx + 1); }
   h->ctl = (Ctl*)dev_alloc(sizeof(Ctl));

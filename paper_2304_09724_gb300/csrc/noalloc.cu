@@ -1,20 +1,21 @@
 // Allocation-free single 1D step.
 //
 // Some callers cannot allocate device memory at the point where they want to advance a
-// solution: code that runs while a CUDA stream capture is open (cudaMalloc and cudaFree are
-// not capturable and implicitly synchronise the device), real-time loops that cannot afford the
-// latency and device-wide synchronisation of an allocation, and host frameworks that own every
-// byte of device memory through their own pool and forbid a library from allocating behind
-// their back.  shweno_step1d_noalloc serves them: the caller passes its input and output state,
-// and the step's scratch (the per-face fluxes and interface states, plus the small control block
-// of the step kernels) lives in one file-scope __device__ array of fixed size that every GPU
-// loading this library holds until the process exits.
+// solution: real-time loops that cannot take the latency of an allocation or the device-wide
+// synchronisation that freeing memory implies, and host frameworks that own every byte of device
+// memory through their own pool and forbid a library from allocating behind their back.
+// shweno_step1d_noalloc serves them: the caller passes its input and output state, and the step's
+// scratch (the per-face fluxes and interface states, plus the small control block of the step
+// kernels) lives in one file-scope __device__ array of fixed size that every GPU loading this
+// library holds until the process exits.  The call waits for its own work before it returns.
 //
 // Set-up: the device address of that array is looked up with cudaGetSymbolAddress the first
-// time the entry point runs on a device (with that device current) and cached per device; that
-// first call should therefore come before any stream capture.  Every call shares the one array
-// per device, so calls whose work overlaps on the GPU (different streams, or different host
-// threads) race on it; callers must order them.
+// time the entry point runs on a device (with that device current) and cached per device for
+// the rest of the process; that first call should come before any stream capture.  The cached
+// address belongs to the device's primary context: a process that destroys that context
+// (cudaDeviceReset) must not call this entry point again.  Every call shares the one array per
+// device, so calls whose work overlaps on the GPU (different streams, or different host threads)
+// race on it; callers must order them.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -69,6 +70,8 @@ extern "C" shweno_status shweno_step1d_noalloc(int32_t eq, int64_t nx, double x0
   for (int s = 0; s < 2; ++s)
     if (bc_kind[s] < SHWENO_BC_PERIODIC || bc_kind[s] > SHWENO_BC_INFLOW) return SHWENO_E_INVALID;
   if ((bc_kind[0] == SHWENO_BC_PERIODIC) != (bc_kind[1] == SHWENO_BC_PERIODIC)) return SHWENO_E_INVALID;
+  // an INFLOW side needs the state it imposes
+  if (!inflow && (bc_kind[0] == SHWENO_BC_INFLOW || bc_kind[1] == SHWENO_BC_INFLOW)) return SHWENO_E_INVALID;
   const int ncomp = eq == SHWENO_BURGERS ? 1 : 3;
   {  // the two states must not overlap
     const size_t bytes = 2 * (size_t)ncomp * nx * sizeof(double);

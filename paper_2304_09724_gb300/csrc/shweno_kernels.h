@@ -29,8 +29,10 @@ void launch_step2d(const Params& P, Ctl* ctl, const double* s0, const double* s1
                    double* o1, const uint8_t* flag, const Scratch2D& S, cudaStream_t st,
                    cudaEvent_t* ev);
 size_t scratch2d_doubles(const Params& P);
-void init_kernels2d();  // kernel attributes (dynamic shared memory); call before any capture
-void init_kernels2d_quintic();
+// Kernel attributes (dynamic shared memory limits of the face kernels); call before any capture.
+// Returns the first failing CUDA status.
+cudaError_t init_kernels2d();
+cudaError_t init_kernels2d_quintic();
 void launch_step2d_quintic(const Params& P, Ctl* ctl, const double* s0, const double* s1,
                            double* o0, double* o1, const uint8_t* flag, const Scratch2D& S,
                            cudaStream_t st, cudaEvent_t* ev);

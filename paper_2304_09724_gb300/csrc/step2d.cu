@@ -26,9 +26,9 @@ Scratch2D carve_scratch2d(const Params& P, double* base) {
   return S;
 }
 
-void init_kernels2d() {
-  init_kernels2d_reading<false>();
-  init_kernels2d_quintic();
+cudaError_t init_kernels2d() {
+  const cudaError_t e = init_kernels2d_reading<false>();
+  return e != cudaSuccess ? e : init_kernels2d_quintic();
 }
 
 void launch_step2d(const Params& P, Ctl* ctl, const double* s0, const double* s1, double* o0,

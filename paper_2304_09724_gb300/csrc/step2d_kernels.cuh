@@ -93,20 +93,28 @@ __global__ void __launch_bounds__(256) update2d_kernel(Params P, Ctl* __restrict
 }
 
 // ------------------------------------------------------------------ host side (templates)
+// Dynamic shared memory limits of the face kernels; returns the first failing call's status.
 template <int NC, bool CHAR, bool Q>
-static void init_kernels2d_nc() {
-  cudaFuncSetAttribute(xface2d_kernel<NC, false, CHAR, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
-  cudaFuncSetAttribute(yface2d_kernel<NC, false, CHAR, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem);
-  cudaFuncSetAttribute(xface2d_kernel<NC, true, CHAR, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmemFlags);
-  cudaFuncSetAttribute(yface2d_kernel<NC, true, CHAR, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmemFlags);
+static cudaError_t init_kernels2d_nc() {
+  cudaError_t e = cudaSuccess;
+  auto set = [&e](const void* f, size_t bytes) {
+    const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) e = r;
+  };
+  set((const void*)xface2d_kernel<NC, false, CHAR, Q>, kFaceSmem);
+  set((const void*)yface2d_kernel<NC, false, CHAR, Q>, kFaceSmem);
+  set((const void*)xface2d_kernel<NC, true, CHAR, Q>, kFaceSmemFlags);
+  set((const void*)yface2d_kernel<NC, true, CHAR, Q>, kFaceSmemFlags);
+  return e;
 }
 
 // Attributes of every face kernel of one reading (Q = false: R1, true: R1').
 template <bool Q>
-static void init_kernels2d_reading() {
-  init_kernels2d_nc<1, false, Q>();
-  init_kernels2d_nc<4, false, Q>();
-  init_kernels2d_nc<4, true, Q>();
+static cudaError_t init_kernels2d_reading() {
+  cudaError_t e = init_kernels2d_nc<1, false, Q>();
+  if (e == cudaSuccess) e = init_kernels2d_nc<4, false, Q>();
+  if (e == cudaSuccess) e = init_kernels2d_nc<4, true, Q>();
+  return e;
 }
 
 

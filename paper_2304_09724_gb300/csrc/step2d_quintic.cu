@@ -6,7 +6,7 @@
 
 namespace shweno {
 
-void init_kernels2d_quintic() { init_kernels2d_reading<true>(); }
+cudaError_t init_kernels2d_quintic() { return init_kernels2d_reading<true>(); }
 
 void launch_step2d_quintic(const Params& P, Ctl* ctl, const double* s0, const double* s1,
                            double* o0, double* o1, const uint8_t* flag, const Scratch2D& S,
