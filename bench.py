@@ -546,6 +546,39 @@ def bench_euler1d(args):
                       "dtype": "f64", "data": "synthetic"}), flush=True)
 
 
+def bench_refinement(args):
+    """Opt-in suite (--suite refinement): the design order on the GPU (Example 5.8, Table 5.4).  The
+    isentropic vortex at each --refine-sizes N x N runs to --refine-t with the plain scheme; the
+    density L1 (mean |e|) and L-infinity errors against the exact cell averages of the translated
+    vortex, and the observed order of each refinement (log2 of the error ratio)."""
+    import numpy as np
+    import torch
+
+    from paper_2304_09724_gb300 import shweno as S
+    from paper_2304_09724_gb300 import workloads as WL
+
+    torch.cuda.set_device(0)
+    T = args.refine_t
+    rows = []
+    for n in (int(x) for x in args.refine_sizes.split(",")):
+        wl = WL.vortex(n)
+        sol = S.Solver(2, S.EULER, n, n, wl.domain, wl.bc)
+        sol.set_state(wl.state)
+        t0 = time.perf_counter()
+        t, steps = sol.run(T, CFL)
+        el = time.perf_counter() - t0
+        e = sol.get_state()["W"][0] - wl.exact(T)[0]
+        sol.close()
+        rows.append({"n": n, "t": t, "steps": steps, "seconds": el, "l1": float(np.mean(np.abs(e))),
+                     "linf": float(np.max(np.abs(e)))})
+    for a, b in zip(rows, rows[1:]):
+        r = b["n"] / a["n"]
+        b["order_l1"] = math.log(a["l1"] / b["l1"]) / math.log(r)
+        b["order_linf"] = math.log(a["linf"] / b["linf"]) / math.log(r)
+    print(json.dumps({"suite": "refinement", "workload": f"2D Euler isentropic vortex to T = {T}, CFL {CFL}, plain",
+                      "rows": rows, "dtype": "f64", "data": "synthetic"}), flush=True)
+
+
 def bench_fp64_probe(args):
     """Opt-in suite (--suite fp64-probe): the FP64 pipe's rate for fused multiply-add, multiply and
     add chains, and for the three interleaved, at 4..32 warps per SM (one CTA per SM), in
@@ -575,10 +608,13 @@ def main():
     ap.add_argument("--ref-window", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--suite", default="main", choices=["main", "batched", "learned-run", "euler1d", "fp64-probe"])
+    ap.add_argument("--suite", default="main", choices=["main", "batched", "learned-run", "euler1d", "fp64-probe",
+                                                      "refinement"])
     ap.add_argument("--n1d", type=int, default=4194304, help="euler1d: cells of the 1D problem")
     ap.add_argument("--dmr-nx", type=int, default=1024, help="learned-run: DMR mesh is N x N/4")
     ap.add_argument("--c5-problems", type=int, default=64)
+    ap.add_argument("--refine-sizes", default="128,256,512,1024", help="refinement: mesh sides")
+    ap.add_argument("--refine-t", type=float, default=2.0, help="refinement: final time")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
@@ -586,6 +622,8 @@ def main():
         bench_euler1d(args)
     elif args.suite == "fp64-probe":
         bench_fp64_probe(args)
+    elif args.suite == "refinement":
+        bench_refinement(args)
     elif args.suite == "learned-run":
         bench_learned_run(args)
     elif args.suite == "batched":

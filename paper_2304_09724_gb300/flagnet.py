@@ -70,8 +70,9 @@ def dataset(seeds, **kw):
     return torch.cat([p[0] for p in parts]), torch.cat([p[1] for p in parts])
 
 
-def train(X, y, epochs=6, batch=16384, lr=2e-3, seed=0, log=None):
-    """Adam on the weighted BCE with the library's kernels; returns the parameters (CUDA)."""
+def train(X, y, epochs=6, batch=16384, lr=2e-3, seed=0, log=None, history=None):
+    """Adam on the weighted BCE with the library's kernels; returns (parameters (CUDA), positive-class
+    weight).  history (a list), if given, receives the mean training loss of every epoch."""
     import torch
 
     n = X.shape[0]
@@ -97,7 +98,19 @@ def train(X, y, epochs=6, batch=16384, lr=2e-3, seed=0, log=None):
             tot += float(loss.item()) * xb.shape[0]
         if log:
             log(f"epoch {ep}: mean loss {tot / n:.4f}")
+        if history is not None:
+            history.append(tot / n)
     return params, pw
+
+
+def mean_loss(params, X, y, pw):
+    """Weighted BCE of the network on (X, y), from the library's gradient kernel."""
+    import torch
+
+    grad = torch.empty_like(params)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    S.shweno_mlp_grad(params, X, y, pw, grad, loss)
+    return float(loss.item())
 
 
 def probabilities(params, X):
