@@ -62,8 +62,8 @@ struct BatchCtl {
   int timeout;              // a wait ran out
 };
 
-constexpr size_t kBatchSmem = kFaceSmemFlags > sizeof(double) * 16 * (TYB + 2) * (TX + 2) ?
-                              kFaceSmemFlags : sizeof(double) * 16 * (TYB + 2) * (TX + 2);
+constexpr size_t kBatchSmem = kFaceSmem > sizeof(double) * 16 * (TYB + 2) * (TX + 2) ?
+                              kFaceSmem : sizeof(double) * 16 * (TYB + 2) * (TX + 2);
 constexpr size_t kBatchSmem1D = sizeof(double) * 2 * 3 * (1024 + 1);  // F-hat and W(t+dt) of a tile
 static_assert(kBatchSmem1D <= kBatchSmem, "1D tiles fit the 2D batch's shared memory");
 
@@ -183,7 +183,7 @@ __device__ void do_item(const BatchProblem& B, int kind, long long idx, unsigned
         const int seg = (int)(idx % B.nsegx), r = (int)(idx / B.nsegx);
         const int slice = r < 3 * P.ny ? r / P.ny : 3;
         const int row = r < 3 * P.ny ? r % P.ny : r - 3 * P.ny;
-        const int f0 = seg * SEG;
+        const int f0 = seg * NFACE;
         if (P.ncomp == 1) {
           if (flags) xface_item<1, true>(P, sv, sv.odd ? B.s1 : B.s0, B.S.ycoef, B.flag, B.S.FX, B.S.WX, B.S.WC, f0, row, slice, smem);
           else xface_item<1, false>(P, sv, sv.odd ? B.s1 : B.s0, B.S.ycoef, B.flag, B.S.FX, B.S.WX, B.S.WC, f0, row, slice, smem);
@@ -195,7 +195,7 @@ __device__ void do_item(const BatchProblem& B, int kind, long long idx, unsigned
         const long long k = idx - B.nxitems;
         const int seg = (int)(k % B.nsegy), r = (int)(k / B.nsegy);
         const int slice = r / P.nx, col = r % P.nx;
-        const int f0 = seg * SEG;
+        const int f0 = seg * NFACE;
         if (P.ncomp == 1) {
           if (flags) yface_item<1, true>(P, sv, sv.odd ? B.s1 : B.s0, B.S.xcoef, B.flag, B.S.FY, B.S.WY, f0, col, slice, smem);
           else yface_item<1, false>(P, sv, sv.odd ? B.s1 : B.s0, B.S.xcoef, B.flag, B.S.FY, B.S.WY, f0, col, slice, smem);
@@ -414,8 +414,8 @@ void fill_problem(shweno_batch* b, int p) {
     const int cells_items = (int)(((size_t)nx * ny + BT - 1) / BT);
     B.ncx = (nx + 4 + TX - 1) / TX;
     B.ncy = (ny + 4 + TYB - 1) / TYB;
-    B.nsegx = (nx + 1 + SEG - 1) / SEG;
-    B.nsegy = (ny + 1 + SEG - 1) / SEG;
+    B.nsegx = (nx + 1 + NFACE - 1) / NFACE;
+    B.nsegy = (ny + 1 + NFACE - 1) / NFACE;
     B.nsegu = (nx + BT - 1) / BT;
     B.nxitems = B.nsegx * (3 * ny + ny + 1);
     int k = 0;

@@ -8,6 +8,11 @@ W+ = W_{j+1}, v- = h V_{j-1}, v+ = h V_{j+1}.  With the symmetric combinations
   s = W- + W+, dv = v+ - v-   (even part of p1)   and   a = W+ - W-, sv = v- + v+   (odd part)
 the monomial coefficients of p1 split into c0, c2, c4 (from W0, s, dv) and c1, c3 (from a, sv).
 
+Both end values of one cell share their arithmetic: the normalised Taylor coefficient m of p1 is
+  e_m(+1/2) = U_m + V_m,   e_m(-1/2) = (-1)^m (U_m - V_m),
+where U_m (the terms of the even monomials) is a linear form in (W0, s, dv) and V_m (the odd
+monomials) one in (a, sv) -- (a, sv, v0) for R1'.  ENDU_/ENDV_ hold those forms.
+
 Reading R1' (option): a quintic p1 that also matches v0 = h V_j.  Its even part is R1's (the
 odd monomials do not enter W0, s or dv); its odd part c1, c3, c5 comes from (a, sv, v0).  The
 Q-prefixed constants below are that variant.
@@ -119,6 +124,62 @@ def main():
     lines.append("  }")
     lines.append("  return 0.0;")
     lines.append("}")
+    # even/odd split of the end values: U_m from (W0, s, dv), V_m from (a, sv) (and v0 for R1')
+    lines.append("// Even/odd parts of the end values: e_m(+1/2) = U_m + V_m, e_m(-1/2) = (-1)^m (U_m - V_m),")
+    lines.append("// U_m = ENDU_m_W0 W0 + ENDU_m_s s + ENDU_m_dv dv, V_m = ENDV_m_a a + ENDV_m_sv sv")
+    lines.append("// (R1'; QENDV_m_a a + QENDV_m_sv sv + QENDV_m_v0 v0; U_m is the same).")
+    qc, _, qn, _, _ = derive_quintic()
+    uv_forms = {}
+    for tag, cf, nm, deg in (("", coef, names, 4), ("Q", qc, qn, 5)):
+        for m in range(5):
+            U, V = {}, {}
+            for j in range(m, deg + 1):
+                w = sp.binomial(j, m) * half ** (j - m)
+                tgt = U if j % 2 == 0 else V
+                for v, val in cf[j].items():
+                    tgt[v] = tgt.get(v, 0) + w * val
+            even_vars, odd_vars = nm[:3], nm[3:]
+            assert all(U.get(v, 0) == 0 for v in odd_vars) and all(V.get(v, 0) == 0 for v in even_vars)
+            # the split reproduces the end rows
+            if tag == "":
+                Wm_, W0_, Wp_, vm_, vp_ = data
+                back = {nm[0]: W0_, nm[1]: Wm_ + Wp_, nm[2]: vp_ - vm_, nm[3]: Wp_ - Wm_, nm[4]: vm_ + vp_}
+                eU = sum(U.get(v, 0) * back[v] for v in nm)
+                eV = sum(V.get(v, 0) * back[v] for v in nm)
+                for sg, tg in ((1, "P"), (-1, "M")):
+                    e = sp.expand(eU + sg * eV) * (1 if sg == 1 else (-1) ** m)
+                    assert all(sp.simplify(e.coeff(v) - ends[(tg, m)][v]) == 0 for v in data), (tg, m)
+                for v in even_vars:
+                    lines.append(f"constexpr double ENDU_{m}_{v} = {frac(U.get(v, 0))};")
+            for v in odd_vars:
+                lines.append(f"constexpr double {tag}ENDV_{m}_{v} = {frac(V.get(v, 0))};")
+            uv_forms[(tag, m)] = (U, V, even_vars, odd_vars)
+    # U_m and V_m as functions; a term whose coefficient is zero is left out (x * 0.0 is not
+    # folded away by the compiler), a coefficient of +-1 is folded by the compiler itself
+    lines.append("// U_m(W0, s, dv) and V_m(a, sv) (R1) or V_m(a, sv, v0) (R1') of the end values")
+    lines.append("__host__ __device__ __forceinline__ double end_u(int m, double W0, double s, double dv) {")
+    lines.append("  switch (m) {")
+    for m in range(5):
+        U, _, ev_, _ = uv_forms[("", m)]
+        terms = [f"ENDU_{m}_{n} * {n}" for v, n in zip(ev_, ["W0", "s", "dv"]) if U.get(v, 0) != 0]
+        lines.append(f"    case {m}: return {' + '.join(terms) if terms else '0.0'};")
+    lines.append("  }")
+    lines.append("  return 0.0;")
+    lines.append("}")
+    for tag, nargs in (("", 2), ("Q", 3)):
+        fn = "end_v" if tag == "" else "qend_v"
+        sig = "double a, double sv" + (", double v0" if tag == "Q" else "")
+        lines.append(f"__host__ __device__ __forceinline__ double {fn}(int m, {sig}) {{")
+        lines.append("  switch (m) {")
+        for m in range(5):
+            _, V, _, ov = uv_forms[(tag, m)]
+            d = {v: V.get(v, 0) for v in ov}
+            names_ = ["a", "sv", "v0"][:nargs]
+            terms = [f"{tag}ENDV_{m}_{n} * {n}" for v, n in zip(ov, names_) if d[v] != 0]
+            lines.append(f"    case {m}: return {' + '.join(terms) if terms else '0.0'};")
+        lines.append("  }")
+        lines.append("  return 0.0;")
+        lines.append("}")
     lines.append("// smoothness indicator of p1: beta1 = sum_{i<=j} B_ij c_i c_j (i, j >= 1)")
     for (i, j), val in bq.items():
         lines.append(f"constexpr double BETA_{i}{j} = {frac(val)};")

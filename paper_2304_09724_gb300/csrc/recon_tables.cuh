@@ -92,6 +92,80 @@ __host__ __device__ __forceinline__ double end_dot(int p, const double d[5]) {
   }
   return 0.0;
 }
+// Even/odd parts of the end values: e_m(+1/2) = U_m + V_m, e_m(-1/2) = (-1)^m (U_m - V_m),
+// U_m = ENDU_m_W0 W0 + ENDU_m_s s + ENDU_m_dv dv, V_m = ENDV_m_a a + ENDV_m_sv sv
+// (R1'; QENDV_m_a a + QENDV_m_sv sv + QENDV_m_v0 v0; U_m is the same).
+constexpr double ENDU_0_W0 = (19.0 / 30.0);
+constexpr double ENDU_0_s = (11.0 / 60.0);
+constexpr double ENDU_0_dv = (-1.0 / 20.0);
+constexpr double ENDV_0_a = (3.0 / 8.0);
+constexpr double ENDV_0_sv = (-1.0 / 8.0);
+constexpr double ENDU_1_W0 = -2.0;
+constexpr double ENDU_1_s = 1.0;
+constexpr double ENDU_1_dv = (-1.0 / 4.0);
+constexpr double ENDV_1_a = (5.0 / 8.0);
+constexpr double ENDV_1_sv = (-1.0 / 8.0);
+constexpr double ENDU_2_W0 = -1.0;
+constexpr double ENDU_2_s = (1.0 / 2.0);
+constexpr double ENDU_2_dv = 0.0;
+constexpr double ENDV_2_a = (-3.0 / 8.0);
+constexpr double ENDV_2_sv = (3.0 / 8.0);
+constexpr double ENDU_3_W0 = 2.0;
+constexpr double ENDU_3_s = -1.0;
+constexpr double ENDU_3_dv = (1.0 / 2.0);
+constexpr double ENDV_3_a = (-1.0 / 4.0);
+constexpr double ENDV_3_sv = (1.0 / 4.0);
+constexpr double ENDU_4_W0 = 1.0;
+constexpr double ENDU_4_s = (-1.0 / 2.0);
+constexpr double ENDU_4_dv = (1.0 / 4.0);
+constexpr double ENDV_4_a = 0.0;
+constexpr double ENDV_4_sv = 0.0;
+constexpr double QENDV_0_a = 0.0;
+constexpr double QENDV_0_sv = 0.0;
+constexpr double QENDV_0_v0 = (1.0 / 2.0);
+constexpr double QENDV_1_a = (3.0 / 4.0);
+constexpr double QENDV_1_sv = (-1.0 / 6.0);
+constexpr double QENDV_1_v0 = (-1.0 / 6.0);
+constexpr double QENDV_2_a = (15.0 / 8.0);
+constexpr double QENDV_2_sv = (-3.0 / 8.0);
+constexpr double QENDV_2_v0 = -3.0;
+constexpr double QENDV_3_a = 0.0;
+constexpr double QENDV_3_sv = (1.0 / 6.0);
+constexpr double QENDV_3_v0 = (-1.0 / 3.0);
+constexpr double QENDV_4_a = (-15.0 / 8.0);
+constexpr double QENDV_4_sv = (5.0 / 8.0);
+constexpr double QENDV_4_v0 = (5.0 / 2.0);
+// U_m(W0, s, dv) and V_m(a, sv) (R1) or V_m(a, sv, v0) (R1') of the end values
+__host__ __device__ __forceinline__ double end_u(int m, double W0, double s, double dv) {
+  switch (m) {
+    case 0: return ENDU_0_W0 * W0 + ENDU_0_s * s + ENDU_0_dv * dv;
+    case 1: return ENDU_1_W0 * W0 + ENDU_1_s * s + ENDU_1_dv * dv;
+    case 2: return ENDU_2_W0 * W0 + ENDU_2_s * s;
+    case 3: return ENDU_3_W0 * W0 + ENDU_3_s * s + ENDU_3_dv * dv;
+    case 4: return ENDU_4_W0 * W0 + ENDU_4_s * s + ENDU_4_dv * dv;
+  }
+  return 0.0;
+}
+__host__ __device__ __forceinline__ double end_v(int m, double a, double sv) {
+  switch (m) {
+    case 0: return ENDV_0_a * a + ENDV_0_sv * sv;
+    case 1: return ENDV_1_a * a + ENDV_1_sv * sv;
+    case 2: return ENDV_2_a * a + ENDV_2_sv * sv;
+    case 3: return ENDV_3_a * a + ENDV_3_sv * sv;
+    case 4: return 0.0;
+  }
+  return 0.0;
+}
+__host__ __device__ __forceinline__ double qend_v(int m, double a, double sv, double v0) {
+  switch (m) {
+    case 0: return QENDV_0_v0 * v0;
+    case 1: return QENDV_1_a * a + QENDV_1_sv * sv + QENDV_1_v0 * v0;
+    case 2: return QENDV_2_a * a + QENDV_2_sv * sv + QENDV_2_v0 * v0;
+    case 3: return QENDV_3_sv * sv + QENDV_3_v0 * v0;
+    case 4: return QENDV_4_a * a + QENDV_4_sv * sv + QENDV_4_v0 * v0;
+  }
+  return 0.0;
+}
 // smoothness indicator of p1: beta1 = sum_{i<=j} B_ij c_i c_j (i, j >= 1)
 constexpr double BETA_11 = 1.0;
 constexpr double BETA_12 = 0.0;

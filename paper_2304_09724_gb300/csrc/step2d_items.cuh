@@ -6,70 +6,211 @@
 
 namespace shweno {
 
-constexpr int SEG = 128;       // face points per CTA
-constexpr int SPAN = SEG + 3;  // first-pass evaluations a CTA needs
-constexpr int TX = 32;         // first-pass tile width
+constexpr int SEG = 128;          // threads of a face CTA
+constexpr int NFACE = SEG - 1;    // faces of a face CTA: its threads own the SEG cells next to them
+constexpr int SPAN = NFACE + 3;   // first-pass evaluations a CTA needs
+constexpr int TX = 32;            // first-pass tile width
 
-// ------------------------------------------------------------------ one face point
+// ------------------------------------------------------------------ second pass, cell by cell
 // Second pass across the face.  ev[set*NC+q][k][col] holds the first-pass Taylor coefficients
-// (order k along the face) of a row of stencil columns.  Each cell's weights come from its
-// order-0 data and serve every order (remark ending Section 2.1.2) and both of the cell's faces:
-// they are computed once per cell (cell_mixes) into shared memory.
-struct MixTable {
-  double A[4][SPAN], B[4][SPAN], C[4][SPAN];  // p = A p1 + B p2 + C p3 per (comp, cell column)
-  int lin[SPAN];                               // 1: the cell uses the linear weights (p = p1)
+// (order k along the face) of a row of stencil columns; column c holds the cell whose stencil is
+// columns c-1..c+1.  Each cell's weights come from its order-0 data and serve every order
+// (remark ending Section 2.1.2) and both of the cell's ends, so one thread per cell forms its
+// weights once and then, order by order, the Taylor coefficients across the face at both ends
+// (EndTable); one thread per face then reads the left cell's right end and the right cell's left
+// end.  The two ends of a cell share their arithmetic: with s = W- + W+, a = W+ - W-,
+// dv = v+ - v-, sv = v- + v+, p1's coefficient p at xi = +-1/2 is U_p + V_p and (-1)^p (U_p - V_p)
+// (U_p from the even monomials, V_p from the odd ones; end_u / end_v of recon_tables.cuh).
+struct EndTable {
+  double R[4][5][SEG];  // right end (xi = +1/2) of the cell in column c at slot c - 1: [comp][p][slot]
+  double L[4][5][SEG];  // left end (xi = -1/2)
 };
-
-// The small-stencil terms of the mixed polynomial at the cell's ends, per (comp, cell column):
-// at the right end e0 gains P0 d(W0) - hB d(W-) + hC d(W+), at the left end
-// M0 d(W0) + hB d(W-) - hC d(W+), and at both ends e1 gains BmC d(W0) - B d(W-) + C d(W+)
-// (P0 = 1.5 B + 0.5 C, M0 = 0.5 B + 1.5 C, hB = B / 2, hC = C / 2, BmC = B - C).  The flagged
-// kernels, which reload the weights from shared memory for every tangential order, read these
-// instead of forming them again for each order.
-struct MixExtra {
-  double P0[4][SPAN], M0[4][SPAN], hB[4][SPAN], hC[4][SPAN], BmC[4][SPAN];
+// Flags of the cells next to the faces, for the characteristic-wise path (whose weights belong to
+// each face point): lin[c] = 1 when the cell in column c uses the linear weights.
+struct FlagTable {
+  int lin[SPAN];
 };
 
 constexpr size_t kEvBytes = sizeof(double) * 8 * 5 * SPAN;
-constexpr size_t kFaceSmem = kEvBytes + sizeof(MixTable);
-constexpr size_t kFaceSmemFlags = kFaceSmem + sizeof(MixExtra);  // flagged kernels
+constexpr size_t kFaceSmem = kEvBytes + (sizeof(EndTable) > sizeof(FlagTable) ? sizeof(EndTable) : sizeof(FlagTable));
 
-// Weights of the cells in columns 1..ncols (the cells next to the faces the CTA owns: ncols =
-// faces + 1, SEG + 1 for a full segment).  nl(col) returns whether the cell of column col uses the
-// nonlinear weights.
-// MIX = false (characteristic-wise reconstruction, whose weights belong to each face point):
-// only the flags are recorded.
-template <int NC, bool MIX, bool Q, bool EXTRA, typename FlagOf>
-__device__ __forceinline__ void cell_mixes(const Params& P, const double (*ev)[5][SPAN],
-                                           MixTable& mt, MixExtra* mx, int ncols, FlagOf nl) {
-  for (int it = threadIdx.x; it < (MIX ? NC : 1) * ncols; it += SEG) {
-    const int q = it / ncols, c = 1 + it % ncols;
-    const int nonlinear = nl(c);
-    if (q == 0) mt.lin[c] = !nonlinear;
-    if (!MIX || !nonlinear) continue;
+// Weights of one cell's reconstruction across the face: p = A p1 + B p2 + C p3 per component.
+template <int NC>
+struct CellMix {
+  double A[NC], B[NC], C[NC];
+  bool lin;  // linear weights: p = p1 (A = 1, B = C = 0)
+};
+
+template <int NC, bool Q>
+__device__ __forceinline__ void cell_mix(const Params& P, const double (*ev)[5][SPAN], int c, bool lin,
+                                         CellMix<NC>& m) {
+  m.lin = lin;
+  if (lin) {  // one branch for the whole cell: a warp of linear cells skips the weights
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      m.A[q] = 1.0;
+      m.B[q] = m.C[q] = 0.0;
+    }
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
     const double Wm = ev[q][0][c - 1], W0 = ev[q][0][c], Wp = ev[q][0][c + 1];
     double cf[6];
     p1_coeffs_t<Q>(Wm, W0, Wp, ev[NC + q][0][c - 1], ev[NC + q][0][c], ev[NC + q][0][c + 1], cf);
-    const Mix m = shweno_mix_t<Q>(P, Wm, W0, Wp, cf, 1);
-    mt.A[q][c] = m.A;
-    mt.B[q][c] = m.B;
-    mt.C[q][c] = m.C;
-    if constexpr (EXTRA) {
-      mx->P0[q][c] = 1.5 * m.B + 0.5 * m.C;
-      mx->M0[q][c] = 0.5 * m.B + 1.5 * m.C;
-      mx->hB[q][c] = 0.5 * m.B;
-      mx->hC[q][c] = 0.5 * m.C;
-      mx->BmC[q][c] = m.B - m.C;
-    }
+    const Mix mm = shweno_mix_t<Q>(P, Wm, W0, Wp, cf, 1);
+    m.A[q] = mm.A;
+    m.B[q] = mm.B;
+    m.C[q] = mm.C;
   }
 }
 
-// Cross-face Taylor coefficients e[p] (p <= 4 - k) of tangential order k, component q, of the
-// cell in column c0 + 1 (stencil c0..c0+2), at its right end (PLUS, xi = +1/2) or left end:
-//   e[p] = A * END[p] . data + (small-stencil terms for p <= 1),
-// with END the constant rows of p1's Taylor coefficients at the end and data = (W-, W0, W+,
-// v-, v+) of order k.
-// d = (W-, W0, W+, v-, v+) for reading R1, (W-, W0, W+, v-, v0, v+) for R1' (Q).
+// Taylor coefficients p = 0..4-K across the face of tangential order K at both ends of the cell in
+// column c, into slot c - 1 of the EndTable.  The small stencils p2 = W0 + (W0 - W-) xi and
+// p3 = W0 + (W+ - W0) xi add h +- g/2 to the value and g to the slope at the ends, with
+// h = (B + C) W0 and g = B (W0 - W-) + C (W+ - W0).  LIN: a cell with the linear weights (p = p1,
+// A = 1, B = C = 0; the general form gives the same values bit for bit with more operations).
+template <int NC, bool LIN, bool Q, int K>
+__device__ __forceinline__ void cell_ends_t(const double (*ev)[5][SPAN], int c, const CellMix<NC>& m,
+                                            EndTable& et) {
+  using namespace shweno_tables;
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    const double Wm = ev[q][K][c - 1], W0 = ev[q][K][c], Wp = ev[q][K][c + 1];
+    const double vm = ev[NC + q][K][c - 1], vp = ev[NC + q][K][c + 1];
+    const double v0 = Q ? ev[NC + q][K][c] : 0.0;
+    const double s = Wm + Wp, a = Wp - Wm, dv = vp - vm, sv = vm + vp;
+    const double A = m.A[q];
+    double g = 0.0, hR = 0.0, hL = 0.0;
+    if (!LIN) {
+      g = m.B[q] * (W0 - Wm) + m.C[q] * (Wp - W0);
+      const double h = (m.B[q] + m.C[q]) * W0;
+      hR = fma(0.5, g, h);
+      hL = fma(-0.5, g, h);
+    }
+#pragma unroll
+    for (int p = 0; p + K <= 4; ++p) {
+      const double U = end_u(p, W0, s, dv);
+      double eR, eL;
+      if (!Q && p == 4) {  // V_4 = 0 for the quartic: both ends are U_4
+        eR = eL = LIN ? U : A * U;
+      } else {
+        const double V = Q ? qend_v(p, a, sv, v0) : end_v(p, a, sv);
+        if (LIN) {
+          eR = U + V;
+          eL = (p & 1) ? V - U : U - V;
+        } else if (p == 0) {
+          eR = fma(A, V, fma(A, U, hR));
+          eL = fma(-A, V, fma(A, U, hL));
+        } else if (p == 1) {
+          eR = fma(A, V, fma(A, U, g));
+          eL = fma(A, V, fma(-A, U, g));
+        } else {
+          const double AU = A * U;
+          eR = fma(A, V, AU);
+          eL = (p & 1) ? fma(A, V, -AU) : fma(-A, V, AU);
+        }
+      }
+      et.R[q][p][c - 1] = eR;
+      et.L[q][p][c - 1] = eL;
+    }
+  }
+}
+// FLAGS = false: every cell is nonlinear (no branch on the flag); otherwise one branch per cell.
+template <int NC, bool FLAGS, bool Q, int K>
+__device__ __forceinline__ void cell_ends(const double (*ev)[5][SPAN], int c, const CellMix<NC>& m,
+                                          EndTable& et) {
+  if (FLAGS && m.lin) cell_ends_t<NC, true, Q, K>(ev, c, m, et);
+  else cell_ends_t<NC, false, Q, K>(ev, c, m, et);
+}
+
+// Order K of the face point between cell columns f + 1 and f + 2: the two sides from the
+// EndTable; at K = 0 the leading term (Burgers: exact Godunov state; Euler: HLLC) and the
+// eigen-decomposition of the upwinding; every derivative vector upwinded into a[q][m*5+n]
+// (m along x, n along y; dir = 0: x-face, p across = m; dir = 1: y-face, p across = n).
+template <int NC, int K>
+__device__ __forceinline__ void face_order(const Params& P, const EndTable& et, int f, int dir,
+                                           double Ws[NC], Upwinder<NC>& U, double a[NC][25]) {
+  double dl[NC][5], dr[NC][5];
+#pragma unroll
+  for (int q = 0; q < NC; ++q)
+#pragma unroll
+    for (int p = 0; p + K <= 4; ++p) {
+      dl[q][p] = et.R[q][p][f];
+      dr[q][p] = et.L[q][p][f + 1];
+    }
+  if constexpr (K == 0) {
+    double WL[NC], WR[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) { WL[q] = dl[q][0]; WR[q] = dr[q][0]; }
+    if constexpr (NC == 1) Ws[0] = burgers_godunov(WL[0], WR[0]);  // the same flux u^2/2 along x and y
+    else hllc_state<NC>(WL, WR, P.gamma, dir, Ws);
+    U.setup(Ws, P.gamma, dir, NC == 1 ? fmax(fabs(WL[0]), fabs(WR[0])) : 0.0);
+  }
+#pragma unroll
+  for (int p = 0; p + K <= 4; ++p) {
+    if (p == 0 && K == 0) continue;
+    double x[NC], y[NC], o[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) { x[q] = dl[q][p]; y[q] = dr[q][p]; }
+    U.apply(x, y, o);
+    const int idx = dir == 0 ? p * 5 + K : K * 5 + p;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) a[q][idx] = o[q];
+  }
+}
+
+// One order of the two-phase second pass: every cell thread writes its ends, then every face
+// thread upwinds them.  Called by all threads of the CTA (it holds the barriers).
+template <int NC, bool FLAGS, bool Q, int K>
+__device__ __forceinline__ void pass_order(const Params& P, const double (*ev)[5][SPAN], EndTable& et,
+                                           bool has_cell, const CellMix<NC>& m, bool has_face,
+                                           int dir, double Ws[NC], Upwinder<NC>& U, double a[NC][25]) {
+  if (has_cell) cell_ends<NC, FLAGS, Q, K>(ev, threadIdx.x + 1, m, et);
+  __syncthreads();
+  if (has_face) face_order<NC, K>(P, et, threadIdx.x, dir, Ws, U, a);
+  __syncthreads();
+}
+
+// Second pass, leading term, upwinding and CK of the nf faces of a CTA (nf <= NFACE): thread t
+// owns the cell in column t + 1 (t <= nf) and the face between columns t + 1 and t + 2 (t < nf).
+// Returns true for a face thread, whose tc[q][0..4] are then the time-Taylor coefficients of its
+// face point.  nl(c): whether the cell in column c uses the nonlinear weights.
+template <int NC, bool FLAGS, bool Q, typename FlagOf>
+__device__ __forceinline__ bool second_pass_cells(const Params& P, const double (*ev)[5][SPAN],
+                                                  unsigned char* tbl, int nf, int dir, FlagOf nl,
+                                                  double tc[NC][5]) {
+  EndTable& et = *reinterpret_cast<EndTable*>(tbl);
+  const bool has_cell = (int)threadIdx.x <= nf, has_face = (int)threadIdx.x < nf;
+  CellMix<NC> m;
+  if (has_cell) cell_mix<NC, Q>(P, ev, threadIdx.x + 1, FLAGS && !nl(threadIdx.x + 1), m);
+  double a[NC][25], Ws[NC];
+  Upwinder<NC> U;
+  pass_order<NC, FLAGS, Q, 0>(P, ev, et, has_cell, m, has_face, dir, Ws, U, a);
+  pass_order<NC, FLAGS, Q, 1>(P, ev, et, has_cell, m, has_face, dir, Ws, U, a);
+  pass_order<NC, FLAGS, Q, 2>(P, ev, et, has_cell, m, has_face, dir, Ws, U, a);
+  pass_order<NC, FLAGS, Q, 3>(P, ev, et, has_cell, m, has_face, dir, Ws, U, a);
+  pass_order<NC, FLAGS, Q, 4>(P, ev, et, has_cell, m, has_face, dir, Ws, U, a);
+  if (!has_face) return false;
+#pragma unroll
+  for (int q = 0; q < NC; ++q) a[q][0] = Ws[q];
+  double t4[NC][5];
+  if constexpr (NC == 1) ck_burgers2d(a, t4, P.ckx, P.cky, P.gamma - 1.0);
+  else ck_euler2d(a, t4, P.ckx, P.cky, P.gamma - 1.0);
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    tc[q][0] = Ws[q];
+#pragma unroll
+    for (int k = 1; k < 5; ++k) tc[q][k] = t4[q][k];
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------ characteristic-wise face point
+// Cross-face Taylor coefficients e[p] (p <= 4 - k) of tangential order k at the right end
+// (PLUS, xi = +1/2) or left end of a cell, from its field data d = (W-, W0, W+, v-, v+) of that
+// order ((W-, W0, W+, v-, v0, v+) for reading R1', Q): e[p] = A * END[p] . d + (small-stencil
+// terms for p <= 1).
 template <bool PLUS, bool Q = false>
 __device__ __forceinline__ void side_out_d(const double* d, int k, double A, double B, double C,
                                            bool lin, double e[5]) {
@@ -85,50 +226,6 @@ __device__ __forceinline__ void side_out_d(const double* d, int k, double A, dou
   if (PLUS) e[0] += (1.5 * B + 0.5 * C) * d[1] - 0.5 * B * d[0] + 0.5 * C * d[2];
   else e[0] += (0.5 * B + 1.5 * C) * d[1] + 0.5 * B * d[0] - 0.5 * C * d[2];
   if (k <= 3) e[1] += (B - C) * d[1] - B * d[0] + C * d[2];
-}
-// side_out_d with the small-stencil coefficients precomputed (MixExtra): e0 gains
-// x1 d(W0) + x0 d(W-) + x2 d(W+) and e1 gains y1 d(W0) + y0 d(W-) + y2 d(W+).
-template <bool PLUS, bool Q = false>
-__device__ __forceinline__ void side_out_pre(const double* d, int k, double A, double x1, double x0,
-                                             double x2, double y1, double y0, double y2, bool lin,
-                                             double e[5]) {
-  using namespace shweno_tables;
-  if (lin) {
-#pragma unroll
-    for (int p = 0; p + k <= 4; ++p) e[p] = Q ? qend_dot<PLUS>(p, d) : end_dot<PLUS>(p, d);
-    return;
-  }
-#pragma unroll
-  for (int p = 0; p + k <= 4; ++p) e[p] = A * (Q ? qend_dot<PLUS>(p, d) : end_dot<PLUS>(p, d));
-  e[0] += x1 * d[1] + x0 * d[0] + x2 * d[2];
-  if (k <= 3) e[1] += y1 * d[1] + y0 * d[0] + y2 * d[2];
-}
-template <int NC, bool PLUS, bool Q = false>
-__device__ __forceinline__ void side_out_x(const double (*ev)[5][SPAN], int c0, int q, int k, double A,
-                                           double x1, double x0, double x2, double y1, double y0,
-                                           double y2, bool lin, double e[5]) {
-  if constexpr (Q) {
-    const double d[6] = {ev[q][k][c0], ev[q][k][c0 + 1], ev[q][k][c0 + 2], ev[NC + q][k][c0],
-                         ev[NC + q][k][c0 + 1], ev[NC + q][k][c0 + 2]};
-    side_out_pre<PLUS, true>(d, k, A, x1, x0, x2, y1, y0, y2, lin, e);
-  } else {
-    const double d[5] = {ev[q][k][c0], ev[q][k][c0 + 1], ev[q][k][c0 + 2], ev[NC + q][k][c0],
-                         ev[NC + q][k][c0 + 2]};
-    side_out_pre<PLUS>(d, k, A, x1, x0, x2, y1, y0, y2, lin, e);
-  }
-}
-template <int NC, bool PLUS, bool Q = false>
-__device__ __forceinline__ void side_out(const double (*ev)[5][SPAN], int c0, int q, int k, double A,
-                                         double B, double C, bool lin, double e[5]) {
-  if constexpr (Q) {
-    const double d[6] = {ev[q][k][c0], ev[q][k][c0 + 1], ev[q][k][c0 + 2], ev[NC + q][k][c0],
-                         ev[NC + q][k][c0 + 1], ev[NC + q][k][c0 + 2]};
-    side_out_d<PLUS, true>(d, k, A, B, C, lin, e);
-  } else {
-    const double d[5] = {ev[q][k][c0], ev[q][k][c0 + 1], ev[q][k][c0 + 2], ev[NC + q][k][c0],
-                         ev[NC + q][k][c0 + 2]};
-    side_out_d<PLUS>(d, k, A, B, C, lin, e);
-  }
 }
 
 // Characteristic-wise counterpart for one face point (Euler, NC = 4): the first-pass data of
@@ -185,26 +282,25 @@ __device__ __forceinline__ void char_sides(const CharBasis<NC>& Bs, const double
   }
 }
 
-// Face point: both sides' second pass, leading term (Burgers: exact Godunov state; Euler:
-// HLLC), upwinding, CK; returns the time-Taylor coefficients tc[q][0..4].  Left cell in column
-// c0 + 1, right cell in c0 + 2.  dir = 0: x-face (first pass along y), 1: y-face.  NC = 1
-// (Burgers, F = G = u^2/2) or 4 (Euler).  CHAR: the second pass runs in the characteristic
-// fields of the Jacobian along the face normal at Wref (the mean of the cell averages next to
-// the point), with its own weights per field and side (the MixTable then holds only the flags).
-template <int NC, bool FLAGS, bool CHAR = false, bool Q = false>
-__device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5][SPAN],
-                                           const MixTable& mt, const MixExtra* mx, int c0, int dir,
-                                           double tc[NC][5], const double* Wref = nullptr) {
-  static_assert(!CHAR || NC == 4, "characteristic fields are for the Euler system");
+// Face point of the characteristic-wise option (Euler): the second pass across the face runs in
+// the characteristic fields of the Jacobian along the face normal at Wref (the mean of the cell
+// averages next to the point), with its own weights per field and side; then the leading term
+// (HLLC), the upwinding and CK.  Left cell in column c0 + 1, right cell in c0 + 2; dir = 0:
+// x-face (first pass along y), 1: y-face.  Returns the time-Taylor coefficients tc[q][0..4].
+template <int NC, bool FLAGS, bool Q>
+__device__ __forceinline__ void char_face_point(const Params& P, const double (*ev)[5][SPAN],
+                                                const FlagTable& ft, int c0, int dir, double tc[NC][5],
+                                                const double* Wref) {
+  static_assert(NC == 4, "characteristic fields are for the Euler system");
   const double g = P.gamma;
   double a[NC][25];
   double dl[NC][5], dr[NC][5];
   double AL[NC], BL[NC], CL[NC], AR[NC], BR[NC], CR[NC];
   // FLAGS = false: every cell uses the nonlinear weights (compile-time, no branch)
-  const bool linL = FLAGS && mt.lin[c0 + 1], linR = FLAGS && mt.lin[c0 + 2];
+  const bool linL = FLAGS && ft.lin[c0 + 1], linR = FLAGS && ft.lin[c0 + 2];
   CharBasis<NC> Bs;
-  if constexpr (CHAR) {
-    Bs.setup(Wref, g, dir);
+  Bs.setup(Wref, g, dir);
+  {
     double xw[4][NC], xv[4][NC];
     fields_at<NC>(ev, Bs, c0, 0, xw, xv);
 #pragma unroll
@@ -225,70 +321,19 @@ __device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5
       }
     }
     char_sides<NC, Q>(Bs, xw, xv, 0, AL, BL, CL, linL, AR, BR, CR, linR, dl, dr);
-  } else {
-#pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      AL[q] = linL ? 1.0 : mt.A[q][c0 + 1]; BL[q] = linL ? 0.0 : mt.B[q][c0 + 1]; CL[q] = linL ? 0.0 : mt.C[q][c0 + 1];
-      AR[q] = linR ? 1.0 : mt.A[q][c0 + 2]; BR[q] = linR ? 0.0 : mt.B[q][c0 + 2]; CR[q] = linR ? 0.0 : mt.C[q][c0 + 2];
-    }
-    // tangential order 0 first: it carries the leading-term data
-#pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      side_out<NC, true, Q>(ev, c0, q, 0, AL[q], BL[q], CL[q], linL, dl[q]);
-      side_out<NC, false, Q>(ev, c0 + 1, q, 0, AR[q], BR[q], CR[q], linR, dr[q]);
-    }
   }
   double WL[NC], WR[NC], Ws[NC];
 #pragma unroll
   for (int q = 0; q < NC; ++q) { WL[q] = dl[q][0]; WR[q] = dr[q][0]; }
-  if constexpr (NC == 1) Ws[0] = burgers_godunov(WL[0], WR[0]);  // the same flux u^2/2 along x and y
-  else hllc_state<NC>(WL, WR, g, dir, Ws);
+  hllc_state<NC>(WL, WR, g, dir, Ws);
   Upwinder<NC> U;
-  U.setup(Ws, g, dir, NC == 1 ? fmax(fabs(WL[0]), fabs(WR[0])) : 0.0);
+  U.setup(Ws, g, dir);
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     if (k > 0) {
-      if constexpr (CHAR) {
-        double xw[4][NC], xv[4][NC];
-        fields_at<NC>(ev, Bs, c0, k, xw, xv);
-        char_sides<NC, Q>(Bs, xw, xv, k, AL, BL, CL, linL, AR, BR, CR, linR, dl, dr);
-      } else {
-        if constexpr (FLAGS) {
-          // the flagged instantiation reloads the weights and the small-stencil coefficients
-          // from shared memory for every order (measured: faster for it; the plain one is 3 %
-          // faster keeping the weights in registers)
-          const volatile double* vA = &mt.A[0][0];
-          const volatile double* vB = &mt.B[0][0];
-          const volatile double* vC = &mt.C[0][0];
-          const volatile double* vP0 = &mx->P0[0][0];
-          const volatile double* vM0 = &mx->M0[0][0];
-          const volatile double* vhB = &mx->hB[0][0];
-          const volatile double* vhC = &mx->hC[0][0];
-          const volatile double* vBmC = &mx->BmC[0][0];
-#pragma unroll
-          for (int q = 0; q < NC; ++q) {
-            const int l = q * SPAN + c0 + 1, r = l + 1;
-            if (linL) {
-              side_out_x<NC, true, Q>(ev, c0, q, k, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, true, dl[q]);
-            } else {
-              side_out_x<NC, true, Q>(ev, c0, q, k, vA[l], vP0[l], -vhB[l], vhC[l], vBmC[l], -vB[l],
-                                      vC[l], false, dl[q]);
-            }
-            if (linR) {
-              side_out_x<NC, false, Q>(ev, c0 + 1, q, k, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, true, dr[q]);
-            } else {
-              side_out_x<NC, false, Q>(ev, c0 + 1, q, k, vA[r], vM0[r], vhB[r], -vhC[r], vBmC[r], -vB[r],
-                                       vC[r], false, dr[q]);
-            }
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < NC; ++q) {
-            side_out<NC, true, Q>(ev, c0, q, k, AL[q], BL[q], CL[q], linL, dl[q]);
-            side_out<NC, false, Q>(ev, c0 + 1, q, k, AR[q], BR[q], CR[q], linR, dr[q]);
-          }
-        }
-      }
+      double xw[4][NC], xv[4][NC];
+      fields_at<NC>(ev, Bs, c0, k, xw, xv);
+      char_sides<NC, Q>(Bs, xw, xv, k, AL, BL, CL, linL, AR, BR, CR, linR, dl, dr);
     }
 #pragma unroll
     for (int p = 0; p + k <= 4; ++p) {
@@ -306,8 +351,7 @@ __device__ __forceinline__ void face_point(const Params& P, const double (*ev)[5
 #pragma unroll
   for (int q = 0; q < NC; ++q) a[q][0] = Ws[q];
   double t4[NC][5];
-  if constexpr (NC == 1) ck_burgers2d(a, t4, P.ckx, P.cky, g - 1.0);
-  else ck_euler2d(a, t4, P.ckx, P.cky, g - 1.0);
+  ck_euler2d(a, t4, P.ckx, P.cky, g - 1.0);
 #pragma unroll
   for (int q = 0; q < NC; ++q) {
     tc[q][0] = Ws[q];
@@ -416,8 +460,8 @@ __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv,
 }
 
 // x-face Gauss points (slice 0..2, cell row `row`) or corner points (slice 3, corner row `row`
-// at y_{row-1/2}) of faces x_{f0-1/2} .. x_{f0+SEG-3/2}; SEG threads, smem_raw of kFaceSmem bytes
-// (kFaceSmemFlags for the flagged kernels).
+// at y_{row-1/2}) of faces x_{f0-1/2} .. x_{f0+NFACE-3/2}; SEG threads, smem_raw of kFaceSmem
+// bytes.
 template <int NC, bool FLAGS, bool CHAR = false, bool Q = false>
 __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv, const double* st,
                                            const double* __restrict__ ycoef,
@@ -425,11 +469,10 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv, 
                                            double* __restrict__ WX, double* __restrict__ WC, int f0,
                                            int row, int slice, unsigned char* smem_raw) {
   double(*ev)[5][SPAN] = reinterpret_cast<double(*)[5][SPAN]>(smem_raw);
-  MixTable& mt = *reinterpret_cast<MixTable*>(smem_raw + kEvBytes);
   const int NX4 = P.nx + 4, NY2 = P.ny + 2;
   using namespace shweno_tables;
   // faces x_{f0-1/2} .. x_{f0+nf-3/2} exist; their stencils span columns 0 .. nf + 2
-  const int nf = min(SEG, P.nx + 1 - f0), ncol = nf + 3;
+  const int nf = min(NFACE, P.nx + 1 - f0), ncol = nf + 3;
   for (int it = threadIdx.x; it < 2 * NC * ncol; it += SEG) {
     const int col = it % ncol, rq = it / ncol;
     const int tcol = f0 + col;
@@ -473,18 +516,19 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv, 
   }
   __syncthreads();
   // cell column c holds cell i = f0 + c - 2; a corner row uses the rows below and above
-  MixExtra* mx = FLAGS && !CHAR ? reinterpret_cast<MixExtra*>(smem_raw + kFaceSmem) : nullptr;
-  cell_mixes<NC, !CHAR, Q, FLAGS && !CHAR>(P, ev, mt, mx, nf + 1, [&](int c) {
+  auto nl = [&](int c) {
     const int i = f0 + c - 2;
     return slice < 3 ? cell_flag(P, flag, i, row)
                      : (cell_flag(P, flag, i, row - 1) | cell_flag(P, flag, i, row));
-  });
-  __syncthreads();
+  };
   const int fi = f0 + threadIdx.x;  // face x_{fi-1/2}
-  if (fi > P.nx) return;  // no barrier follows
   double tc[NC][5];
-  double Wref[NC];
-  if constexpr (CHAR) {  // cells next to the face point (the four around a corner)
+  if constexpr (CHAR) {
+    FlagTable& ft = *reinterpret_cast<FlagTable*>(smem_raw + kEvBytes);
+    for (int c = 1 + threadIdx.x; c <= nf + 1; c += SEG) ft.lin[c] = !nl(c);
+    __syncthreads();
+    if ((int)threadIdx.x >= nf) return;  // no barrier follows
+    double Wref[NC];  // cells next to the face point (the four around a corner)
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
       if (slice < 3)
@@ -493,8 +537,10 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv, 
         Wref[q] = 0.25 * (fetch(P, st, 0, q, fi - 1, row - 1, sv.t) + fetch(P, st, 0, q, fi, row - 1, sv.t) +
                           fetch(P, st, 0, q, fi - 1, row, sv.t) + fetch(P, st, 0, q, fi, row, sv.t));
     }
+    char_face_point<NC, FLAGS, Q>(P, ev, ft, threadIdx.x, 0, tc, Wref);
+  } else {
+    if (!second_pass_cells<NC, FLAGS, Q>(P, ev, smem_raw + kEvBytes, nf, 0, nl, tc)) return;
   }
-  face_point<NC, FLAGS, CHAR, Q>(P, ev, mt, mx, threadIdx.x, 0, tc, Wref);
   const double dt = sv.dt;
   if (slice < 3) {
     double Fh[NC], We[NC];
@@ -511,7 +557,7 @@ __device__ __forceinline__ void xface_item(const Params& P, const StepView& sv, 
   }
 }
 
-// y-face Gauss points (slice 0..2) of column `col`, faces y_{f0-1/2} .. y_{f0+SEG-3/2}.
+// y-face Gauss points (slice 0..2) of column `col`, faces y_{f0-1/2} .. y_{f0+NFACE-3/2}.
 template <int NC, bool FLAGS, bool CHAR = false, bool Q = false>
 __device__ __forceinline__ void yface_item(const Params& P, const StepView& sv, const double* st,
                                            const double* __restrict__ xcoef,
@@ -519,11 +565,10 @@ __device__ __forceinline__ void yface_item(const Params& P, const StepView& sv, 
                                            double* __restrict__ WY, int f0, int col, int slice,
                                            unsigned char* smem_raw) {
   double(*ev)[5][SPAN] = reinterpret_cast<double(*)[5][SPAN]>(smem_raw);
-  MixTable& mt = *reinterpret_cast<MixTable*>(smem_raw + kEvBytes);
   const int NY4 = P.ny + 4;
   using namespace shweno_tables;
   // faces y_{f0-1/2} .. y_{f0+nf-3/2} exist; their stencils span rows 0 .. nf + 2
-  const int nf = min(SEG, P.ny + 1 - f0), nrow = nf + 3;
+  const int nf = min(NFACE, P.ny + 1 - f0), nrow = nf + 3;
   for (int it = threadIdx.x; it < 2 * NC * nrow; it += SEG) {
     const int r = it % nrow, rq = it / nrow;
     const int trow = f0 + r;
@@ -543,20 +588,22 @@ __device__ __forceinline__ void yface_item(const Params& P, const StepView& sv, 
     for (int k = 0; k < 5; ++k) ev[rq][k][r] = e[k];
   }
   __syncthreads();
-  MixExtra* mx = FLAGS && !CHAR ? reinterpret_cast<MixExtra*>(smem_raw + kFaceSmem) : nullptr;
-  cell_mixes<NC, !CHAR, Q, FLAGS && !CHAR>(P, ev, mt, mx, nf + 1,
-                                           [&](int c) { return cell_flag(P, flag, col, f0 + c - 2); });
-  __syncthreads();
+  auto nl = [&](int c) { return cell_flag(P, flag, col, f0 + c - 2); };
   const int fj = f0 + threadIdx.x;  // face y_{fj-1/2}
-  if (fj > P.ny) return;
   double tc[NC][5];
-  double Wref[NC];
   if constexpr (CHAR) {
+    FlagTable& ft = *reinterpret_cast<FlagTable*>(smem_raw + kEvBytes);
+    for (int c = 1 + threadIdx.x; c <= nf + 1; c += SEG) ft.lin[c] = !nl(c);
+    __syncthreads();
+    if ((int)threadIdx.x >= nf) return;
+    double Wref[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q)
       Wref[q] = 0.5 * (fetch(P, st, 0, q, col, fj - 1, sv.t) + fetch(P, st, 0, q, col, fj, sv.t));
+    char_face_point<NC, FLAGS, Q>(P, ev, ft, threadIdx.x, 1, tc, Wref);
+  } else {
+    if (!second_pass_cells<NC, FLAGS, Q>(P, ev, smem_raw + kEvBytes, nf, 1, nl, tc)) return;
   }
-  face_point<NC, FLAGS, CHAR, Q>(P, ev, mt, mx, threadIdx.x, 1, tc, Wref);
   double Gh[NC], We[NC];
   lobatto<NC>(tc, sv.dt, P.gamma, 1, Gh, We);
 #pragma unroll

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(SEG) xface2d_kernel(Params P, const Ctl* __res
   const int row = blockIdx.y;    // Gauss: cell row j; corner: corner row jc (y_{jc-1/2})
   if (slice < 3 && row >= P.ny) return;
   const StepView sv = step_view(ctl);
-  xface_item<NC, FLAGS, CHAR, Q>(P, sv, sv.odd ? s1 : s0, ycoef, flag, FX, WX, WC, blockIdx.x * SEG, row, slice,
+  xface_item<NC, FLAGS, CHAR, Q>(P, sv, sv.odd ? s1 : s0, ycoef, flag, FX, WX, WC, blockIdx.x * NFACE, row, slice,
                               smem_raw);
 }
 
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(SEG) yface2d_kernel(Params P, const Ctl* __res
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (!ctl->active) return;
   const StepView sv = step_view(ctl);
-  yface_item<NC, FLAGS, CHAR, Q>(P, sv, sv.odd ? s1 : s0, xcoef, flag, FY, WY, blockIdx.x * SEG, blockIdx.y,
+  yface_item<NC, FLAGS, CHAR, Q>(P, sv, sv.odd ? s1 : s0, xcoef, flag, FY, WY, blockIdx.x * NFACE, blockIdx.y,
                               blockIdx.z, smem_raw);
 }
 
@@ -103,8 +103,8 @@ static cudaError_t init_kernels2d_nc() {
   };
   set((const void*)xface2d_kernel<NC, false, CHAR, Q>, kFaceSmem);
   set((const void*)yface2d_kernel<NC, false, CHAR, Q>, kFaceSmem);
-  set((const void*)xface2d_kernel<NC, true, CHAR, Q>, kFaceSmemFlags);
-  set((const void*)yface2d_kernel<NC, true, CHAR, Q>, kFaceSmemFlags);
+  set((const void*)xface2d_kernel<NC, true, CHAR, Q>, kFaceSmem);
+  set((const void*)yface2d_kernel<NC, true, CHAR, Q>, kFaceSmem);
   return e;
 }
 
@@ -122,17 +122,17 @@ static cudaError_t init_kernels2d_reading() {
 template <int NC, bool CHAR, bool Q>
 static void launch_faces2d(const Params& P, Ctl* ctl, const double* s0, const double* s1,
                            const uint8_t* flag, const Scratch2D& S, cudaStream_t st, cudaEvent_t* ev) {
-  dim3 xg((P.nx + 1 + SEG - 1) / SEG, P.ny + 1, 4);
+  dim3 xg((P.nx + 1 + NFACE - 1) / NFACE, P.ny + 1, 4);
   if (P.flag_mode == FLAG_ALL_NONLINEAR)
     xface2d_kernel<NC, false, CHAR, Q><<<xg, SEG, kFaceSmem, st>>>(P, ctl, s0, s1, S.ycoef, flag, S.FX, S.WX, S.WC);
   else
-    xface2d_kernel<NC, true, CHAR, Q><<<xg, SEG, kFaceSmemFlags, st>>>(P, ctl, s0, s1, S.ycoef, flag, S.FX, S.WX, S.WC);
+    xface2d_kernel<NC, true, CHAR, Q><<<xg, SEG, kFaceSmem, st>>>(P, ctl, s0, s1, S.ycoef, flag, S.FX, S.WX, S.WC);
   if (ev) cudaEventRecord(ev[2], st);
-  dim3 yg((P.ny + 1 + SEG - 1) / SEG, P.nx, 3);
+  dim3 yg((P.ny + 1 + NFACE - 1) / NFACE, P.nx, 3);
   if (P.flag_mode == FLAG_ALL_NONLINEAR)
     yface2d_kernel<NC, false, CHAR, Q><<<yg, SEG, kFaceSmem, st>>>(P, ctl, s0, s1, S.xcoef, flag, S.FY, S.WY);
   else
-    yface2d_kernel<NC, true, CHAR, Q><<<yg, SEG, kFaceSmemFlags, st>>>(P, ctl, s0, s1, S.xcoef, flag, S.FY, S.WY);
+    yface2d_kernel<NC, true, CHAR, Q><<<yg, SEG, kFaceSmem, st>>>(P, ctl, s0, s1, S.xcoef, flag, S.FY, S.WY);
 }
 
 template <int NC, bool Q>
