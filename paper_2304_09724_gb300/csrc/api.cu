@@ -620,6 +620,15 @@ shweno_status shweno_weight_deviation(shweno_handle* h, double* out) {
   return SHWENO_OK;
 }
 
+shweno_status shweno_face_deviation(shweno_handle* h, double* out) {
+  if (!h || !out) return fail(h, SHWENO_E_INVALID, "null argument");
+  if (h->P.dim != 2 || h->P.eq != SHWENO_EULER) return fail(h, SHWENO_E_STATE, "needs a 2D Euler handle");
+  shweno::launch_fdev2d(h->P, h->ctl, h->buf[0], h->buf[1], out, h->stream);
+  CK(h, cudaGetLastError());
+  CK(h, cudaStreamSynchronize(h->stream));
+  return SHWENO_OK;
+}
+
 shweno_status shweno_mlp_forward(const float* params, const float* x, int64_t n, float* prob,
                                  void* cuda_stream) {
   if (!params || (n > 0 && (!x || !prob)) || n < 0) return SHWENO_E_INVALID;

@@ -7,9 +7,12 @@
 //                for rho and E, the eight 3x3 neighbours minus the centre and dx V, dy Y of the
 //                centre, divided by (stencil range + 1e-12 |centre| + 1e-300), and
 //                log10(range / (|centre| + 1e-30) + 1e-16) / 8.
-//   wdev2d       training label source: per cell, the largest relative deviation
+//   wdev2d       label source: per cell, the largest relative deviation
 //                max_l |w_l - gamma_l| / gamma_l of the 16 first-pass reconstructions anchored
 //                on it (the plain scheme's own weights).
+//   fdev2d       training label source: per cell, the largest change those weights make to the
+//                reconstructions' end values, |p(+-1/2) - p1(+-1/2)|, relative to the range of the
+//                reconstruction's three averages (+ 1e-9 |W0|).
 //   mlp_forward / mlp_grad / mlp_adam   FP32 network 22 -> 32 -> 32 -> 1 (ReLU, ReLU, sigmoid),
 //                binary cross-entropy with a positive-class weight, Adam.
 //   infer2d + dilate2d   each step, before the reconstruction: flag = net(features) > threshold,
@@ -57,6 +60,38 @@ __global__ void wdev2d_kernel(Params P, const Ctl* __restrict__ ctl, const doubl
         // back from (A, B, C) to the weights: w1 = A g1, w2 = B + A g2, w3 = C + A g3
         const double w[3] = {m.A * P.gam[0], m.B + m.A * P.gam[1], m.C + m.A * P.gam[2]};
         for (int l = 0; l < 3; ++l) dev = fmax(dev, fabs(w[l] - P.gam[l]) / P.gam[l]);
+      }
+  out[c] = dev;
+}
+
+__global__ void fdev2d_kernel(Params P, const Ctl* __restrict__ ctl, const double* s0,
+                              const double* s1, double* __restrict__ out) {
+  const size_t cells = (size_t)P.nx * P.ny;
+  const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cells) return;
+  const double* st = (ctl->nsteps & 1) ? s1 : s0;
+  const int i = (int)(c % P.nx), j = (int)(c / P.nx);
+  const double t = ctl->t;
+  double dev = 0.0;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int set = 0; set < 2; ++set)
+      for (int q = 0; q < P.ncomp; ++q) {
+        const int fa = pass == 0 ? (set == 0 ? 0 : 1) : (set == 0 ? 0 : 2);
+        const int fd = pass == 0 ? (set == 0 ? 2 : 3) : (set == 0 ? 1 : 3);
+        const int di = pass == 1, dj = pass == 0;
+        const double h = pass == 0 ? P.dy : P.dx;
+        const double Wm = fetch(P, st, fa, q, i - di, j - dj, t), W0 = fetch(P, st, fa, q, i, j, t);
+        const double Wp = fetch(P, st, fa, q, i + di, j + dj, t);
+        double cf[5];
+        p1_coeffs(Wm, W0, Wp, h * fetch(P, st, fd, q, i - di, j - dj, t), h * fetch(P, st, fd, q, i + di, j + dj, t), cf);
+        const Mix m = shweno_mix(P, Wm, W0, Wp, cf, 1);
+        // p - p1 = (A - 1) p1 + B p2 + C p3 at xi = +-1/2 (p2 = W0 + (W0 - W-) xi, p3 = W0 + (W+ - W0) xi)
+        const double even = cf[0] + 0.25 * cf[2] + 0.0625 * cf[4], odd = 0.5 * cf[1] + 0.125 * cf[3];
+        const double s2 = 0.5 * (W0 - Wm), s3 = 0.5 * (Wp - W0);
+        const double scale = fmax(Wm, fmax(W0, Wp)) - fmin(Wm, fmin(W0, Wp)) + 1e-9 * fabs(W0) + 1e-300;
+        const double dR = (m.A - 1.0) * (even + odd) + m.B * (W0 + s2) + m.C * (W0 + s3);
+        const double dL = (m.A - 1.0) * (even - odd) + m.B * (W0 - s2) + m.C * (W0 - s3);
+        dev = fmax(dev, fmax(fabs(dR), fabs(dL)) / scale);
       }
   out[c] = dev;
 }
@@ -223,6 +258,12 @@ void launch_features2d(const Params& P, const Ctl* ctl, const double* s0, const 
   const size_t cells = (size_t)P.nx * P.ny;
   features2d_kernel<<<(unsigned)((cells + 127) / 128), 128, 0, st>>>(P, ctl, s0, s1, out);
 }
+void launch_fdev2d(const Params& P, const Ctl* ctl, const double* s0, const double* s1,
+                   double* out, cudaStream_t st) {
+  const size_t cells = (size_t)P.nx * P.ny;
+  fdev2d_kernel<<<(unsigned)((cells + 127) / 128), 128, 0, st>>>(P, ctl, s0, s1, out);
+}
+
 void launch_wdev2d(const Params& P, const Ctl* ctl, const double* s0, const double* s1,
                    double* out, cudaStream_t st) {
   const size_t cells = (size_t)P.nx * P.ny;

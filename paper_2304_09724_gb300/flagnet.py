@@ -5,8 +5,10 @@ shweno_mlp_grad, shweno_mlp_adam through the C ABI); PyTorch only holds the devi
 Labels come from the plain scheme itself: seeded random four-quadrant Riemann problems (rho ~
 U[0.1,2], u, v ~ U[-1,1], p ~ U[0.1,2]) at 256 x 256 are advanced with the always-nonlinear
 scheme; at several snapshots every cell gets the features of shweno_flag_features and the label
-1 if shweno_weight_deviation exceeds delta (the nonlinear weights of some reconstruction anchored
-on the cell deviate from the linear ones by more than delta, relatively).
+1 if shweno_face_deviation exceeds DELTA_FACE: the nonlinear weights of some reconstruction
+anchored on the cell move its end values by more than that fraction of the range of its cell
+averages.  (label="weights" keeps the earlier label: shweno_weight_deviation above 0.05, the
+weights themselves deviating from the linear ones by more than 5 %.)
 
     python -m paper_2304_09724_gb300.flagnet --out flagnet_weights.npz
 """
@@ -35,9 +37,15 @@ def init_params(seed):
     return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
 
 
-def snapshot_data(seed, n=256, times=(0.0, 0.05, 0.1, 0.175, 0.25), delta=0.05):
+DELTA_FACE = 1e-3    # label threshold of the face-value form
+DELTA_WEIGHTS = 0.05  # label threshold of the weight form
+
+
+def snapshot_data(seed, n=256, times=(0.0, 0.05, 0.1, 0.175, 0.25), label="face", delta=None):
     """(features [k*cells][22], labels [k*cells], deviations) of one seeded problem (CUDA tensors).
     A problem whose plain run leaves the physical range keeps the snapshots taken before."""
+    if delta is None:
+        delta = DELTA_FACE if label == "face" else DELTA_WEIGHTS
     import torch
 
     wl = WL.riemann2d(n, WL.random_quadrants(seed))
@@ -55,7 +63,7 @@ def snapshot_data(seed, n=256, times=(0.0, 0.05, 0.1, 0.175, 0.25), delta=0.05):
         x = torch.empty((n * n, NIN), dtype=torch.float32, device="cuda")
         d = torch.empty(n * n, dtype=torch.float64, device="cuda")
         S.shweno_flag_features(sol.h, x)
-        S.shweno_weight_deviation(sol.h, d)
+        (S.shweno_face_deviation if label == "face" else S.shweno_weight_deviation)(sol.h, d)
         X.append(x)
         D.append(d)
     sol.close()

@@ -48,7 +48,8 @@ EXPORTS = ["shweno_create", "shweno_set_state", "shweno_get_state", "shweno_step
            "shweno_kernel_name", "shweno_cfl_dt", "shweno_get_time", "shweno_set_flags",
            "shweno_destroy", "shweno_last_error", "shweno_set_allocator", "shweno_step1d_noalloc",
            "shweno_fp64_probe",
-           "shweno_flag_features", "shweno_weight_deviation", "shweno_mlp_forward", "shweno_mlp_grad",
+           "shweno_flag_features", "shweno_weight_deviation", "shweno_face_deviation", "shweno_mlp_forward",
+           "shweno_mlp_grad",
            "shweno_mlp_adam", "shweno_set_flag_net", "shweno_get_flags", "shweno_batch_create",
            "shweno_batch_run", "shweno_batch_autotune", "shweno_batch_set", "shweno_batch_destroy",
            "shweno_batch_last_error"]
@@ -92,6 +93,7 @@ def lib():
     L.shweno_fp64_probe.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, vp, dp, dp]
     L.shweno_flag_features.argtypes = [vp, vp]
     L.shweno_weight_deviation.argtypes = [vp, vp]
+    L.shweno_face_deviation.argtypes = [vp, vp]
     L.shweno_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
     L.shweno_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_float, vp, vp, vp]
     L.shweno_mlp_adam.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
@@ -234,6 +236,11 @@ def shweno_flag_features(h, out):
 def shweno_weight_deviation(h, out):
     """out: CUDA float64 tensor [cells]."""
     _check(lib().shweno_weight_deviation(h, _ptr(out)[0]), h)
+
+
+def shweno_face_deviation(h, out):
+    """out: CUDA float64 tensor [cells]."""
+    _check(lib().shweno_face_deviation(h, _ptr(out)[0]), h)
 
 
 def shweno_mlp_forward(params, x, prob, stream=0):

@@ -32,8 +32,10 @@ def test_features_and_deviation_match_oracle():
     st = sol.get_state()
     x = torch.empty((40 * 40, 22), dtype=torch.float32, device="cuda")
     d = torch.empty(40 * 40, dtype=torch.float64, device="cuda")
+    fd = torch.empty(40 * 40, dtype=torch.float64, device="cuda")
     S.shweno_flag_features(sol.h, x)
     S.shweno_weight_deviation(sol.h, d)
+    S.shweno_face_deviation(sol.h, fd)
     t, _ = sol.time()
     sol.close()
     P = U.problem_of(wl)
@@ -45,6 +47,13 @@ def test_features_and_deviation_match_oracle():
     delta = 0.05
     tie = np.abs(do - delta) < 1e-9
     assert np.array_equal((dg > delta)[~tie], (do > delta)[~tie])
+    # face-value label: the two sides round p - p1 differently, which matters only where the
+    # deviation is at rounding level (about 1e-7 of the scale); the labels agree off ties
+    fg, fo_ = fd.cpu().numpy(), O.face_deviation2d(P, st, t).ravel()
+    np.testing.assert_allclose(fg, fo_, rtol=1e-8, atol=1e-6)
+    assert fo_.max() > 0.1
+    tie = np.abs(fo_ - F.DELTA_FACE) < 1e-6
+    assert np.array_equal((fg > F.DELTA_FACE)[~tie], (fo_ > F.DELTA_FACE)[~tie])
 
 
 def test_network_kernels_match_oracle():

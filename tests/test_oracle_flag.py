@@ -74,3 +74,43 @@ def test_weight_deviation_cases():
     d = O.weight_deviation2d(Pj, wl.state)
     assert d.max() > 1.0  # cells at the quadrant jumps
     assert d[0, 0] == 0.0 and d[9, 9] == 0.0  # corners far from the jumps are constant
+
+
+def test_face_deviation_hand_case_and_limits():
+    """Label source of the face-value form, evaluated by hand.  Step data W = (0, 0, 1), v = (0, 0):
+    p1's end values are 67/120 (xi = +1/2) and -23/120 (xi = -1/2) (rows of the quartic's end
+    values), p2 = 0 and p3 = xi, and with the weights w (evaluated in exact rationals in
+    test_oracle_recon) p = A p1 + B p2 + C p3, A = w1/g1, B = w2 - A g2, C = w3 - A g3, so
+    p - p1 = (A - 1) p1 + C xi at the ends; the range of the averages is 1."""
+    import sympy as sp
+
+    from tests.test_oracle_recon import HAND_CASES, GAM_Q, _exact_weights
+
+    w = _exact_weights(HAND_CASES[0]["beta"])
+    A = w[0] / GAM_Q[0]
+    C = w[2] - A * GAM_Q[2]
+    half = sp.Rational(1, 2)
+    right = (A - 1) * sp.Rational(67, 120) + C * half
+    left = (A - 1) * sp.Rational(-23, 120) - C * half
+    expect = float(max(abs(right), abs(left)))
+    assert O.face_deviation([0.0, 0.0, 1.0], [0.0, 0.0]) == pytest.approx(expect, rel=1e-12)
+    # data of a linear function: all three polynomials coincide, whatever the weights
+    assert O.face_deviation([0.3 - 0.7, 0.3, 0.3 + 0.7], [0.7, 0.7]) < 1e-15
+    # a smooth quadratic barely moves the end values (the weights are close to linear and
+    # p2, p3 differ from p1 by O(h^2)), a step moves them by a large fraction of the range
+    assert O.face_deviation([0.0, 0.1, 0.3], [0.05, 0.25]) < 1e-3 * O.face_deviation([0.0, 0.0, 1.0], [0.0, 0.0])
+
+
+def test_face_deviation2d_cases():
+    """Constant data move no end value (up to rounding, which the 1e-9 |W0| floor of the scale
+    keeps near 1e-7); four-quadrant data move them at the jumps only."""
+    P = O.make_problem(2, 1, 10, 10, bc=(0, 0, 0, 0))
+    assert O.face_deviation2d(P, WL.constant_state(2, 1, 10, 10)).max() < 1e-6
+    wl = WL.riemann2d(10, WL.LAX_LIU_SHOCKS)
+    Pj = O.make_problem(2, 1, 10, 10, *wl.domain, bc=wl.bc)
+    d = O.face_deviation2d(Pj, wl.state)
+    assert d.max() > 0.1 and d[0, 0] < 1e-6 and d[9, 9] < 1e-6
+    # the face-value label is the weight label's companion: at rounding level where the weights
+    # do not move
+    dw = O.weight_deviation2d(Pj, wl.state)
+    assert np.all(d[dw == 0.0] < 1e-6)
