@@ -42,6 +42,66 @@ DRAM_BYTES_PER_XFACE_POINT = 344.3
 BYTES_PER_CELL_UPDATE = 256  # 16 doubles read + 16 written per cell (ideal reuse)
 
 
+def method_flops_per_xface_launch(n):
+    """Floating-point operations of the method itself in one x-face launch of an n x n Euler mesh
+    (3 (n+1) n Gauss points, (n+1)^2 corner points), counted from the formulas each step needs in
+    its minimal form (a fused multiply-add counts 2, a division or square root 1): the denominator
+    that would expose redundant work, beside the kernel's own executed FP64 count.  Per point:
+      first pass   the 2 NC first-pass quartics of the point's column shifted to the point
+                   (10 multiply-adds each; none at the middle Gauss node; a corner averages the
+                   traces of two rows: two shifts and the mean);
+      weights      per component of the cell: p1's coefficients (4 sums, 12 products), beta1
+                   (8 products, 4 sums), beta2, beta3, tau, the three weights and one division;
+      end values   per component, tangential order k and cross order p <= 4 - k of the cell: the
+                   even and odd parts U_p, V_p (their nonzero terms), both ends with the weights
+                   (two fused operations each; one product when V_p = 0), the small stencils'
+                   terms for p <= 1;
+      leading      HLLC: two primitive states, the wave speeds, S*, the star state;
+      upwinding    eigenvectors at the leading term, 14 derivative vectors (difference, one
+                   projection onto the acoustic wave that carries weight, its correction);
+      ck           the generated Cauchy-Kovalevskaya recursion (its own term count);
+      flux         four Lobatto nodes: Horner in time, the physical flux, the weighted sum
+                   (a corner point only evaluates the state at the last node)."""
+    import importlib.util
+
+    NC = 4
+    spec = importlib.util.spec_from_file_location(
+        "gen_ck", os.path.join(ROOT, "paper_2304_09724_gb300", "csrc", "gen_ck.py"))
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    g = gen.Gen(2, "euler")
+    g.emit("ck")
+    ck = g.flops
+    shift = 2 * 10  # one quartic moved to a new centre: 10 multiply-adds
+    first_gauss = 2 * NC * shift * 2 / 3  # two of the three Gauss nodes need the shift
+    first_corner = 2 * NC * (2 * shift + 2 * 5)
+    p1_coeffs = 4 + (5 + 3 + 5 + 3 + 5)  # s, a, dv, sv; c0..c4 (three or two terms each)
+    beta1, beta23, tau = 15, 4, 5
+    mix = 3 + 4 * 3 + 2 + 1 + 2 + 3 + 3  # e_l, the three unnormalised weights, sum, 1/sum, A, B, C
+    weights = NC * (p1_coeffs + beta1 + beta23 + tau + mix)
+    end = 0
+    for k in range(5):
+        end += 4 + 11  # the symmetric sums, g and h with their halves
+        for p in range(5 - k):
+            u = 5 if p != 2 else 3
+            v = 3 if p != 4 else 0
+            both = 8 if p <= 1 else (4 + 1 if p < 4 else 1)
+            end += u + v + both
+    end *= NC
+    prim = 1 + 2 + 6 + 2 + 3
+    leading = 2 * prim + 4 + 4 + 8 + 14
+    upwind = prim + 40 + 14 * (NC + (2 * NC - 1) + 2 * NC)
+    flux = 4 * (NC * 2 * 4 + (1 + 14) + NC * 2)
+    at_corner = NC * 2 * 4
+    common = weights + end + leading + upwind + ck
+    per_gauss = first_gauss + common + flux
+    per_corner = first_corner + common + at_corner
+    total = 3 * (n + 1) * n * per_gauss + (n + 1) ** 2 * per_corner
+    parts = {"first_pass_gauss": first_gauss, "first_pass_corner": first_corner, "weights": weights,
+             "end_values": end, "leading_term": leading, "upwinding": upwind, "ck": ck, "flux": flux}
+    return total, {k: round(v, 1) for k, v in parts.items()}
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -231,22 +291,9 @@ def learned_vs_plain(S, torch, WL, steps, warmup, vortex_wl):
     return out
 
 
-def bench_batched(args):
-    """Opt-in suite (--suite batched): the two batched workloads.
-    1D: 512 seeded Riemann problems (rho ~ U[0.1,2], u ~ U[-1,1], p ~ U[0.1,10], jump at 1/2,
-        outflow, N ~ U{400..16384}) in one persistent launch with autotuned tiles, `steps` steps
-        per problem, against advancing the handles one after another.
-    2D: 64 seeded four-quadrant problems (sides 512..2048), `steps` steps per problem, plain and
-        learned flag in one persistent launch each, against the plain per-instance solver."""
-    import numpy as np
-    import torch
-
-    from paper_2304_09724_gb300 import flagnet as F
-    from paper_2304_09724_gb300 import shweno as S
-    from paper_2304_09724_gb300 import workloads as WL
-
-    torch.cuda.set_device(0)
-    out = {"suite": "batched", "steps_per_problem": args.steps, "dtype": "f64", "data": "synthetic"}
+def _batch_tools(S, torch):
+    """Helpers of the batched measurements: handles from workloads, cell-updates since a
+    snapshot, one timed batch run, the handles advanced one after another."""
 
     def make(wls, learned=False, net=None):
         sols = []
@@ -263,23 +310,26 @@ def bench_batched(args):
     def updates(sols, before):
         return sum(s.nx * s.ny * (s.time()[1] - b) for s, b in zip(sols, before))
 
-    def timed_batch(sols, T, tune):
+    def timed_batch(sols, T, steps, tune):
         b = S.Batch(sols)
         tuned = b.autotune(T, CFL, trial_steps=2) if tune else None
         before = [s.time()[1] for s in sols]
-        t0 = time.perf_counter()
-        st, per = b.run(T, CFL, max_steps=args.steps, check=False)
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            t0 = time.perf_counter()
+            st, per = b.run(T, CFL, max_steps=steps, check=False)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
         n = updates(sols, before)
         b.close()
-        return n / el, el, tuned, per
+        return n / el, el, tuned, per, clk.summary()
 
-    def timed_solo(sols):
+    def timed_solo(sols, steps):
         before = [s.time()[1] for s in sols]
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         for s in sols:
-            S.shweno_advance(s.h, args.steps, CFL)
+            S.shweno_advance(s.h, steps, CFL)
         for s in sols:
             try:
                 S.shweno_sync(s.h)
@@ -288,31 +338,50 @@ def bench_batched(args):
         el = time.perf_counter() - t0
         return updates(sols, before) / el, el
 
-    # ---- 1D
+    return make, updates, timed_batch, timed_solo
+
+
+def batched_1d(S, torch, WL, steps):
+    """512 seeded 1D Riemann problems (rho ~ U[0.1,2], u ~ U[-1,1], p ~ U[0.1,10], jump at 1/2,
+    outflow, N ~ U{400..16384}, end time 0.15) in one persistent launch with autotuned tiles,
+    `steps` steps per problem, against the same handles advanced one after another."""
+    make, _, timed_batch, timed_solo = _batch_tools(S, torch)
     wls = [WL.random_riemann1d(s) for s in range(512)]
     sols = make(wls)
-    rate_b, el_b, tuned, per = timed_batch(sols, 0.15, True)
+    rate_b, el_b, tuned, per, clk = timed_batch(sols, 0.15, steps, True)
     for s in sols:
         s.close()
     sols = make(wls)
-    rate_s, el_s = timed_solo(sols)
+    rate_s, el_s = timed_solo(sols, steps)
     for s in sols:
         s.close()
-    out["batched_1d_riemann_512"] = {
-        "cells": int(sum(w.nx for w in wls)), "batch_cell_updates_per_s": rate_b, "batch_s": el_b,
-        "per_instance_cell_updates_per_s": rate_s, "per_instance_s": el_s, "speedup": rate_b / rate_s,
-        "autotuned": {"tile1d": tuned[0], "ctas_per_sm": tuned[1]},
-        "nonphysical_problems": int(sum(1 for x in per if x == S.E_NONPHYSICAL))}
-    del wls
-    # ---- 2D
+    return {"workload": "512 1D Euler Riemann problems, N ~ U{400..16384}, FP64, CFL 0.6",
+            "cells": int(sum(w.nx for w in wls)), "steps_per_problem": steps,
+            "batch_cell_updates_per_s": rate_b, "batch_s": el_b,
+            "per_instance_cell_updates_per_s": rate_s, "per_instance_s": el_s, "speedup": rate_b / rate_s,
+            "autotuned": {"tile1d": tuned[0], "ctas_per_sm": tuned[1]},
+            "nonphysical_problems": int(sum(1 for x in per if x == S.E_NONPHYSICAL)), "clocks": clk}
+
+
+def batched_2d(S, torch, WL, steps, problems):
+    """`problems` seeded four-quadrant 2D Riemann problems (rho ~ U[0.1,2], u, v ~ U[-1,1],
+    p ~ U[0.1,2], sides 512..2048, end time 0.25): `steps` steps per problem, plain and learned
+    flag in one persistent launch each, against the plain handles advanced one after another."""
+    import numpy as np
+
+    from paper_2304_09724_gb300 import flagnet as F
+
+    make, _, timed_batch, timed_solo = _batch_tools(S, torch)
     net = F.load()
-    wls = [WL.random_riemann2d(s) for s in range(args.c5_problems)]
-    res = {"problems": len(wls), "cells": int(sum(w.nx * w.ny for w in wls))}
+    wls = [WL.random_riemann2d(s) for s in range(problems)]
+    res = {"workload": f"{problems} 2D Euler four-quadrant Riemann problems, sides 512..2048, FP64, CFL 0.6",
+           "problems": len(wls), "cells": int(sum(w.nx * w.ny for w in wls)), "steps_per_problem": steps}
     for mode in ("plain", "learned"):
         sols = make(wls, learned=(mode == "learned"), net=net)
-        r, el, _, per = timed_batch(sols, 0.25, False)
+        r, el, _, per, clk = timed_batch(sols, 0.25, steps, False)
         res[f"batch_{mode}_cell_updates_per_s"] = r
         res[f"batch_{mode}_s"] = el
+        res[f"batch_{mode}_clocks"] = clk
         res[f"nonphysical_problems_{mode}"] = int(sum(1 for x in per if x == S.E_NONPHYSICAL))
         if mode == "learned":
             fr = []
@@ -324,12 +393,27 @@ def bench_batched(args):
         for s in sols:
             s.close()
     sols = make(wls)
-    r, el = timed_solo(sols)
+    r, el = timed_solo(sols, steps)
     for s in sols:
         s.close()
     res["per_instance_plain_cell_updates_per_s"] = r
     res["per_instance_plain_s"] = el
-    out["batched_2d_quadrants"] = res
+    res["batch_plain_vs_per_instance"] = res["batch_plain_cell_updates_per_s"] / r
+    res["batch_learned_vs_per_instance"] = res["batch_learned_cell_updates_per_s"] / r
+    return res
+
+
+def bench_batched(args):
+    """Opt-in suite (--suite batched): the two batched workloads with --steps steps per problem."""
+    import torch
+
+    from paper_2304_09724_gb300 import shweno as S
+    from paper_2304_09724_gb300 import workloads as WL
+
+    torch.cuda.set_device(0)
+    out = {"suite": "batched", "steps_per_problem": args.steps, "dtype": "f64", "data": "synthetic",
+           "batched_1d_riemann_512": batched_1d(S, torch, WL, args.steps),
+           "batched_2d_quadrants": batched_2d(S, torch, WL, args.steps, args.c5_problems)}
     print(json.dumps(out), flush=True)
 
 
@@ -413,8 +497,14 @@ def bench_gpu(args):
     if dom == "xface2d" and FLOPS_PER_XFACE_POINT:
         flops = FLOPS_PER_XFACE_POINT * xpoints
         ach = flops / (dom_ms / 1000.0) / 1e12
+        mflops, mparts = method_flops_per_xface_launch(n)
+        mach = mflops / (dom_ms / 1000.0) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": DRAM_BYTES_PER_XFACE_POINT * xpoints,
+                # the same launch counted by the method's own operations (minimal forms), not the
+                # kernel's executed instructions: work the kernel repeats would lower this fraction
+                "method": {"flops_per_launch": mflops, "flops_per_point": mflops / xpoints,
+                           "per_point_parts": mparts, "achieved": mach, "frac": mach / FP64_PEAK_TFLOPS},
                 "flops_per_launch": flops, "launch_ms": dom_ms,
                 "fp64_pipe_slot_frac": FP64_INST_PER_XFACE_POINT * xpoints / (dom_ms / 1000.0) / FP64_SLOTS_PER_S,
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe)",
@@ -441,7 +531,12 @@ def bench_gpu(args):
         "gpu_launches": 3 + 6 * args.steps,
     }
     if not args.no_learned:
-        line["learned_flag"] = learned_vs_plain(S, torch, WL, args.steps, args.warmup, wl)
+        with ClockSampler(local) as clk_l:
+            line["learned_flag"] = learned_vs_plain(S, torch, WL, args.steps, args.warmup, wl)
+        line["learned_flag"]["clocks"] = clk_l.summary()
+    if not args.no_batched:
+        line["batched_1d"] = batched_1d(S, torch, WL, args.c4_steps)
+        line["batched_2d"] = batched_2d(S, torch, WL, args.c5_steps, args.c5_problems)
     if not args.no_cpu_baseline:
         rate, el = oracle_sample(wl, args.cpu_window, 1)
         line["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
@@ -550,7 +645,9 @@ def bench_refinement(args):
     """Opt-in suite (--suite refinement): the design order on the GPU (Example 5.8, Table 5.4).  The
     isentropic vortex at each --refine-sizes N x N runs to --refine-t with the plain scheme; the
     density L1 (mean |e|) and L-infinity errors against the exact cell averages of the translated
-    vortex, and the observed order of each refinement (log2 of the error ratio)."""
+    vortex over the whole box and over its core (cells within 2.5 of the vortex centre, which the
+    acoustic waves shed by the seams of the periodic data reach only after about t = 1.5), and the
+    observed order of each refinement."""
     import numpy as np
     import torch
 
@@ -569,12 +666,14 @@ def bench_refinement(args):
         el = time.perf_counter() - t0
         e = sol.get_state()["W"][0] - wl.exact(T)[0]
         sol.close()
+        core = WL.vortex_core_mask(n, T)
         rows.append({"n": n, "t": t, "steps": steps, "seconds": el, "l1": float(np.mean(np.abs(e))),
-                     "linf": float(np.max(np.abs(e)))})
+                     "linf": float(np.max(np.abs(e))), "core_l1": float(np.mean(np.abs(e[core]))),
+                     "core_linf": float(np.max(np.abs(e[core])))})
     for a, b in zip(rows, rows[1:]):
         r = b["n"] / a["n"]
-        b["order_l1"] = math.log(a["l1"] / b["l1"]) / math.log(r)
-        b["order_linf"] = math.log(a["linf"] / b["linf"]) / math.log(r)
+        for k in ("l1", "linf", "core_l1", "core_linf"):
+            b["order_" + k] = math.log(a[k] / b[k]) / math.log(r)
     print(json.dumps({"suite": "refinement", "workload": f"2D Euler isentropic vortex to T = {T}, CFL {CFL}, plain",
                       "rows": rows, "dtype": "f64", "data": "synthetic"}), flush=True)
 
@@ -608,13 +707,16 @@ def main():
     ap.add_argument("--ref-window", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="main line without the batched workloads")
+    ap.add_argument("--c4-steps", type=int, default=10, help="steps per problem of the 1D batch on the main line")
+    ap.add_argument("--c5-steps", type=int, default=2, help="steps per problem of the 2D batch on the main line")
     ap.add_argument("--suite", default="main", choices=["main", "batched", "learned-run", "euler1d", "fp64-probe",
                                                       "refinement"])
     ap.add_argument("--n1d", type=int, default=4194304, help="euler1d: cells of the 1D problem")
     ap.add_argument("--dmr-nx", type=int, default=1024, help="learned-run: DMR mesh is N x N/4")
     ap.add_argument("--c5-problems", type=int, default=64)
     ap.add_argument("--refine-sizes", default="128,256,512,1024", help="refinement: mesh sides")
-    ap.add_argument("--refine-t", type=float, default=2.0, help="refinement: final time")
+    ap.add_argument("--refine-t", type=float, default=1.0, help="refinement: final time")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)

@@ -7,8 +7,10 @@ limiter in the scheme) and the library stops at the same step as the oracle.
 Behind the Shu-Osher shock the componentwise scheme amplifies rounding differences between two
 correct FP64 implementations by about 100x per 0.2 time units (measured: rel L1 of W 2e-16 at
 t = 0.05, 4e-13 at 0.4, 7e-11 at 0.6, 4e-6 at 1.8; the characteristic-wise option stays at 1e-15
-to t = 0.6).  The parity bar therefore holds to t = 0.4; the full run to T = 1.8 is checked
-against the bound that growth allows."""
+to t = 0.6).  The parity bar therefore holds to t = 0.4.  The full run to T = 1.8 is held to the
+oracle's own drift: the oracle run from initial data perturbed by a relative 1e-15 (three seeded
+sign patterns) ends 4e-7 ... 5e-6 (rel L1) from the unperturbed oracle run, and the library must
+end within 10x the largest of those from it."""
 import numpy as np
 import pytest
 
@@ -30,12 +32,20 @@ def test_shock_examples_parity(maker, T):
     U.check(g, o, U.fields(wl), shocked=True, what=wl.name, wl=wl)
 
 
-def test_shu_osher_full_run_within_rounding_growth():
+def test_shu_osher_full_run_within_the_oracles_own_drift():
     wl = WL.shu_osher(400)
     g, o, (t, n), (t_o, n_o) = U.run_both(wl, wl.t_final)
     assert n == n_o and t == t_o == wl.t_final
-    rel = np.sum(np.abs(g["W"] - o["W"])) / np.sum(np.abs(o["W"]))
-    assert rel < 1e-4, rel
+    P = U.problem_of(wl)
+    drift = []
+    for seed in (1, 2, 3):
+        rng = np.random.default_rng(seed)
+        st = {k: v * (1.0 + 1e-15 * rng.choice([-1.0, 1.0], size=v.shape)) for k, v in wl.state.items()}
+        op, n_p, _ = O.run(P, st, wl.t_final, wl.cfl)
+        assert n_p == n_o
+        drift.append(U.rel_l1(op["W"], o["W"]))
+    rel = U.rel_l1(g["W"], o["W"])
+    assert rel <= 10.0 * max(drift), (rel, drift)
 
 
 def test_blast_waves_conservation_on_gpu():
