@@ -36,9 +36,9 @@ FP64_SLOTS_PER_S = 152 * 2 * 2.070e9  # FP64 thread instructions per second (DFM
 # pipe slot) per x-face point of xface2d, from ncu's instruction counters of the current kernel on
 # the 2048^2 launch, and its DRAM bytes per point from a capture at 512^2 (traffic grows in
 # proportion to the points).
-FLOPS_PER_XFACE_POINT = 5746.5
-FP64_INST_PER_XFACE_POINT = 3320.0
-DRAM_BYTES_PER_XFACE_POINT = 344.3
+FLOPS_PER_XFACE_POINT = 5105.4
+FP64_INST_PER_XFACE_POINT = 3018.0
+DRAM_BYTES_PER_XFACE_POINT = 306.8
 BYTES_PER_CELL_UPDATE = 256  # 16 doubles read + 16 written per cell (ideal reuse)
 
 

@@ -198,9 +198,11 @@ shweno_status shweno_weight_deviation(shweno_handle* h, double* out);
 /* Training-label source of the face-value form: per cell, the largest change the plain scheme's
  * nonlinear weights make to the end values of those 16 first-pass reconstructions (reading R1),
  *   max over reconstructions and xi = -1/2, +1/2 of |p(xi) - p1(xi)| / (max - min of the
- *   reconstruction's three averages + 1e-9 |W0| + 1e-300),
- * with p the SHWENO polynomial and p1 the big-stencil quartic (Section 2.4).  out[cells]. */
-shweno_status shweno_face_deviation(shweno_handle* h, double* out);
+ *   reconstruction's three averages + floor_rel |W0| + 1e-300),
+ * with p the SHWENO polynomial and p1 the big-stencil quartic (Section 2.4).  floor_rel >= 1e-9
+ * (1e-9: relative to the local range; larger values discount changes that are small against the
+ * cell's own average).  out[cells].  Errors: INVALID (floor_rel), STATE (not 2D Euler). */
+shweno_status shweno_face_deviation(shweno_handle* h, double floor_rel, double* out);
 
 /* Network on n samples: prob[b] = sigmoid(net(x[b])).  x: [n][SHWENO_FLAG_FEATURES]. */
 shweno_status shweno_mlp_forward(const float* params, const float* x, int64_t n, float* prob,

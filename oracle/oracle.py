@@ -86,8 +86,8 @@ def lib():
         L.orc_run.restype = ctypes.c_int64
         L.orc_weight_deviation2d.argtypes = [pp, dp, dp, dp, dp, ctypes.c_double, dp]
         L.orc_features2d.argtypes = [pp, dp, dp, dp, dp, ctypes.c_double, dp]
-        L.orc_face_deviation2d.argtypes = [pp, dp, dp, dp, dp, ctypes.c_double, dp]
-        L.orc_face_deviation.argtypes = [dp, dp, ctypes.c_double, dp]
+        L.orc_face_deviation2d.argtypes = [pp, dp, dp, dp, dp, ctypes.c_double, ctypes.c_double, dp]
+        L.orc_face_deviation.argtypes = [dp, dp, ctypes.c_double, dp, ctypes.c_double]
         L.orc_face_deviation.restype = ctypes.c_double
         L.orc_step2d_window.argtypes = [pp, dp, dp, dp, dp, u8p, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
@@ -280,18 +280,18 @@ def weight_deviation2d(P, state, t=0.0):
     return out
 
 
-def face_deviation(Wb, v, eps=1e-6, gam=GAMMA_LINEAR):
-    """max over xi = -1/2, +1/2 of |p(xi) - p1(xi)| / (range of Wb + 1e-9 |W0| + 1e-300) for the
-    reconstruction of the middle cell (v = (h V_-1, h V_+1))."""
-    return lib().orc_face_deviation(_dp(_f64(Wb)), _dp(_f64(v)), eps, _dp(_f64(gam)))
+def face_deviation(Wb, v, eps=1e-6, gam=GAMMA_LINEAR, floor_rel=1e-9):
+    """max over xi = -1/2, +1/2 of |p(xi) - p1(xi)| / (range of Wb + floor_rel |W0| + 1e-300) for
+    the reconstruction of the middle cell (v = (h V_-1, h V_+1))."""
+    return lib().orc_face_deviation(_dp(_f64(Wb)), _dp(_f64(v)), eps, _dp(_f64(gam)), floor_rel)
 
 
-def face_deviation2d(P, state, t=0.0):
+def face_deviation2d(P, state, t=0.0, floor_rel=1e-9):
     """Per cell: the largest relative change the nonlinear weights make to the end values of its
     16 first-pass reconstructions [ny][nx]."""
     W, V, Y, Z = (_f64(state[k]) for k in "WVYZ")
     out = np.zeros((P.ny, P.nx))
-    lib().orc_face_deviation2d(ctypes.byref(P), _dp(W), _dp(V), _dp(Y), _dp(Z), t, _dp(out))
+    lib().orc_face_deviation2d(ctypes.byref(P), _dp(W), _dp(V), _dp(Y), _dp(Z), t, floor_rel, _dp(out))
     return out
 
 

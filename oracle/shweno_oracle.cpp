@@ -1186,17 +1186,19 @@ void orc_weight_deviation2d(const orc_problem* P, const double* W, const double*
 // Label source of the face-value form: the largest change the nonlinear weights make to the end
 // values of the 16 first-pass reconstructions anchored on cell (i, j), relative to the range of
 // the reconstruction's three cell averages:
-//   max over reconstructions and xi = -1/2, +1/2 of |p(xi) - p1(xi)| / (max Wb - min Wb + 1e-9 |W0| + 1e-300),
+//   max over reconstructions and xi = -1/2, +1/2 of |p(xi) - p1(xi)| / (max Wb - min Wb + f |W0| + 1e-300),
 // where p is the SHWENO polynomial with the nonlinear weights and p1 the big-stencil polynomial
-// (the reconstruction with the linear weights), both of reading R1.  The 1e-9 |W0| keeps rounding
-// (a few ulp of |W0| in p - p1 on constant data) near 1e-7.
-double face_deviation(const double Wb[3], const double v[3], int quintic, double eps, const double gam[3]) {
+// (the reconstruction with the linear weights), both of reading R1, and f >= 1e-9 the caller's
+// floor of the scale relative to the cell's own average (1e-9 keeps rounding, a few ulp of |W0|
+// in p - p1 on constant data, near 1e-7; a larger f discounts changes small against |W0|).
+double face_deviation(const double Wb[3], const double v[3], int quintic, double eps, const double gam[3],
+                      double floor_rel) {
   double w[3], c[6], c1[6];
   shweno_weights(Wb, v, quintic, 0, eps, gam, w);
   shweno_poly(Wb, v, quintic, w, gam, c);
   big_poly(Wb, v, quintic, c1);
   const double mx = std::fmax(Wb[0], std::fmax(Wb[1], Wb[2])), mn = std::fmin(Wb[0], std::fmin(Wb[1], Wb[2]));
-  const double scale = mx - mn + 1e-9 * std::fabs(Wb[1]) + 1e-300;
+  const double scale = mx - mn + floor_rel * std::fabs(Wb[1]) + 1e-300;
   double dev = 0.0;
   for (double xi : {-0.5, 0.5}) {
     double d[5], d1[5];
@@ -1207,7 +1209,7 @@ double face_deviation(const double Wb[3], const double v[3], int quintic, double
   return dev;
 }
 void orc_face_deviation2d(const orc_problem* P, const double* W, const double* V, const double* Y,
-                          const double* Z, double t, double* out) {
+                          const double* Z, double t, double floor_rel, double* out) {
   State S{P, {W, V, Y, Z}, nullptr, t};
   const int nc = ncomp(*P);
   for (int j = 0; j < P->ny; ++j)
@@ -1225,14 +1227,14 @@ void orc_face_deviation2d(const orc_problem* P, const double* W, const double* V
                             fetch(S, fa, q, i + di, j + dj)};
             double v[3] = {h * fetch(S, fd, q, i - di, j - dj), h * fetch(S, fd, q, i, j),
                            h * fetch(S, fd, q, i + di, j + dj)};
-            dev = std::fmax(dev, face_deviation(Wb, v, 0, P->eps, P->gam));  // reading R1's polynomials
+            dev = std::fmax(dev, face_deviation(Wb, v, 0, P->eps, P->gam, floor_rel));  // reading R1's polynomials
           }
       out[(size_t)j * P->nx + i] = dev;
     }
 }
-double orc_face_deviation(const double* Wb, const double* v, double eps, const double* gam) {
+double orc_face_deviation(const double* Wb, const double* v, double eps, const double* gam, double floor_rel) {
   const double v3[3] = {v[0], 0.0, v[1]};
-  return face_deviation(Wb, v3, 0, eps, gam);
+  return face_deviation(Wb, v3, 0, eps, gam, floor_rel);
 }
 
 // Features of cell (i, j), 11 per variable for rho (component 0) and E (last component):

@@ -620,10 +620,11 @@ shweno_status shweno_weight_deviation(shweno_handle* h, double* out) {
   return SHWENO_OK;
 }
 
-shweno_status shweno_face_deviation(shweno_handle* h, double* out) {
+shweno_status shweno_face_deviation(shweno_handle* h, double floor_rel, double* out) {
   if (!h || !out) return fail(h, SHWENO_E_INVALID, "null argument");
+  if (!(floor_rel >= 1e-9) || !std::isfinite(floor_rel)) return fail(h, SHWENO_E_INVALID, "floor_rel must be >= 1e-9");
   if (h->P.dim != 2 || h->P.eq != SHWENO_EULER) return fail(h, SHWENO_E_STATE, "needs a 2D Euler handle");
-  shweno::launch_fdev2d(h->P, h->ctl, h->buf[0], h->buf[1], out, h->stream);
+  shweno::launch_fdev2d(h->P, h->ctl, h->buf[0], h->buf[1], floor_rel, out, h->stream);
   CK(h, cudaGetLastError());
   CK(h, cudaStreamSynchronize(h->stream));
   return SHWENO_OK;

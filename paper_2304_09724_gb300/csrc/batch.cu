@@ -62,10 +62,10 @@ struct BatchCtl {
   int timeout;              // a wait ran out
 };
 
-constexpr size_t kBatchSmem = kFaceSmem > sizeof(double) * 16 * (TYB + 2) * (TX + 2) ?
-                              kFaceSmem : sizeof(double) * 16 * (TYB + 2) * (TX + 2);
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t kBatchSmem1D = sizeof(double) * 2 * 3 * (1024 + 1);  // F-hat and W(t+dt) of a tile
-static_assert(kBatchSmem1D <= kBatchSmem, "1D tiles fit the 2D batch's shared memory");
+// the largest item: a face segment, a first-pass tile (16 fields with halo) or a 1D tile
+constexpr size_t kBatchSmem = cmax(cmax(kFaceSmem, sizeof(double) * 16 * (TYB + 2) * (TX + 2)), kBatchSmem1D);
 
 __device__ __forceinline__ long long enc(int p, int ph, long long idx) {
   return ((long long)p << 40) | ((long long)ph << 36) | idx;

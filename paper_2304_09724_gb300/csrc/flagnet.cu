@@ -12,7 +12,7 @@
 //                on it (the plain scheme's own weights).
 //   fdev2d       training label source: per cell, the largest change those weights make to the
 //                reconstructions' end values, |p(+-1/2) - p1(+-1/2)|, relative to the range of the
-//                reconstruction's three averages (+ 1e-9 |W0|).
+//                reconstruction's three averages plus the caller's floor times |W0|.
 //   mlp_forward / mlp_grad / mlp_adam   FP32 network 22 -> 32 -> 32 -> 1 (ReLU, ReLU, sigmoid),
 //                binary cross-entropy with a positive-class weight, Adam.
 //   infer2d + dilate2d   each step, before the reconstruction: flag = net(features) > threshold,
@@ -65,7 +65,7 @@ __global__ void wdev2d_kernel(Params P, const Ctl* __restrict__ ctl, const doubl
 }
 
 __global__ void fdev2d_kernel(Params P, const Ctl* __restrict__ ctl, const double* s0,
-                              const double* s1, double* __restrict__ out) {
+                              const double* s1, double floor_rel, double* __restrict__ out) {
   const size_t cells = (size_t)P.nx * P.ny;
   const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= cells) return;
@@ -88,7 +88,7 @@ __global__ void fdev2d_kernel(Params P, const Ctl* __restrict__ ctl, const doubl
         // p - p1 = (A - 1) p1 + B p2 + C p3 at xi = +-1/2 (p2 = W0 + (W0 - W-) xi, p3 = W0 + (W+ - W0) xi)
         const double even = cf[0] + 0.25 * cf[2] + 0.0625 * cf[4], odd = 0.5 * cf[1] + 0.125 * cf[3];
         const double s2 = 0.5 * (W0 - Wm), s3 = 0.5 * (Wp - W0);
-        const double scale = fmax(Wm, fmax(W0, Wp)) - fmin(Wm, fmin(W0, Wp)) + 1e-9 * fabs(W0) + 1e-300;
+        const double scale = fmax(Wm, fmax(W0, Wp)) - fmin(Wm, fmin(W0, Wp)) + floor_rel * fabs(W0) + 1e-300;
         const double dR = (m.A - 1.0) * (even + odd) + m.B * (W0 + s2) + m.C * (W0 + s3);
         const double dL = (m.A - 1.0) * (even - odd) + m.B * (W0 - s2) + m.C * (W0 - s3);
         dev = fmax(dev, fmax(fabs(dR), fabs(dL)) / scale);
@@ -259,9 +259,9 @@ void launch_features2d(const Params& P, const Ctl* ctl, const double* s0, const 
   features2d_kernel<<<(unsigned)((cells + 127) / 128), 128, 0, st>>>(P, ctl, s0, s1, out);
 }
 void launch_fdev2d(const Params& P, const Ctl* ctl, const double* s0, const double* s1,
-                   double* out, cudaStream_t st) {
+                   double floor_rel, double* out, cudaStream_t st) {
   const size_t cells = (size_t)P.nx * P.ny;
-  fdev2d_kernel<<<(unsigned)((cells + 127) / 128), 128, 0, st>>>(P, ctl, s0, s1, out);
+  fdev2d_kernel<<<(unsigned)((cells + 127) / 128), 128, 0, st>>>(P, ctl, s0, s1, floor_rel, out);
 }
 
 void launch_wdev2d(const Params& P, const Ctl* ctl, const double* s0, const double* s1,

@@ -42,7 +42,7 @@ void launch_features2d(const Params& P, const Ctl* ctl, const double* s0, const 
 void launch_wdev2d(const Params& P, const Ctl* ctl, const double* s0, const double* s1,
                    double* out, cudaStream_t st);
 void launch_fdev2d(const Params& P, const Ctl* ctl, const double* s0, const double* s1,
-                   double* out, cudaStream_t st);
+                   double floor_rel, double* out, cudaStream_t st);
 void launch_infer2d(const Params& P, const Ctl* ctl, const double* s0, const double* s1,
                     const float* params, float logit_thr, uint8_t* raw, uint8_t* flags,
                     cudaStream_t st);

@@ -38,17 +38,21 @@ def init_params(seed):
 
 
 DELTA_FACE = 1e-3    # label threshold of the face-value form
+FACE_FLOOR = 1e-9    # floor of its scale, relative to the cell's own average
 DELTA_WEIGHTS = 0.05  # label threshold of the weight form
 
 
-def snapshot_data(seed, n=256, times=(0.0, 0.05, 0.1, 0.175, 0.25), label="face", delta=None):
-    """(features [k*cells][22], labels [k*cells], deviations) of one seeded problem (CUDA tensors).
+def snapshot_data(seed, n=256, times=(0.0, 0.05, 0.1, 0.175, 0.25), label="face", delta=None,
+                  kind="quadrants", keep=1.0):
+    """(features [k*cells][22], labels [k*cells], deviations) of one seeded problem (CUDA tensors):
+    kind "quadrants" a four-quadrant Riemann problem, "smooth" a smooth periodic flow
+    (workloads.smooth_flow_2d); keep < 1 keeps that fraction of each snapshot's cells (seeded).
     A problem whose plain run leaves the physical range keeps the snapshots taken before."""
     if delta is None:
         delta = DELTA_FACE if label == "face" else DELTA_WEIGHTS
     import torch
 
-    wl = WL.riemann2d(n, WL.random_quadrants(seed))
+    wl = WL.riemann2d(n, WL.random_quadrants(seed)) if kind == "quadrants" else WL.smooth_flow_2d(seed, n)
     sol = S.Solver(2, S.EULER, n, n, wl.domain, wl.bc, flag_mode=0)
     sol.set_state(wl.state)
     X, D = [], []
@@ -63,7 +67,15 @@ def snapshot_data(seed, n=256, times=(0.0, 0.05, 0.1, 0.175, 0.25), label="face"
         x = torch.empty((n * n, NIN), dtype=torch.float32, device="cuda")
         d = torch.empty(n * n, dtype=torch.float64, device="cuda")
         S.shweno_flag_features(sol.h, x)
-        (S.shweno_face_deviation if label == "face" else S.shweno_weight_deviation)(sol.h, d)
+        if label == "face":
+            S.shweno_face_deviation(sol.h, d, FACE_FLOOR)
+        else:
+            S.shweno_weight_deviation(sol.h, d)
+        if keep < 1.0:
+            g = torch.Generator(device="cuda")
+            g.manual_seed(seed * 7919 + len(X))
+            idx = torch.randperm(n * n, device="cuda", generator=g)[: int(keep * n * n)]
+            x, d = x[idx], d[idx]
         X.append(x)
         D.append(d)
     sol.close()
@@ -75,6 +87,21 @@ def dataset(seeds, **kw):
     import torch
 
     parts = [snapshot_data(s, **kw) for s in seeds]
+    return torch.cat([p[0] for p in parts]), torch.cat([p[1] for p in parts])
+
+
+SMOOTH_SIZES = (128, 256, 512, 1024)
+
+
+def smooth_dataset(seeds, times=(0.0, 0.05), **kw):
+    """Smooth periodic flows at the mesh sizes SMOOTH_SIZES in turn, each snapshot thinned to
+    about 65536 cells: the fine-mesh smooth data that the quadrant problems at 256^2 lack."""
+    import torch
+
+    parts = []
+    for k, s in enumerate(seeds):
+        n = SMOOTH_SIZES[k % len(SMOOTH_SIZES)]
+        parts.append(snapshot_data(s, n=n, times=times, kind="smooth", keep=min(1.0, 65536 / (n * n)), **kw))
     return torch.cat([p[0] for p in parts]), torch.cat([p[1] for p in parts])
 
 

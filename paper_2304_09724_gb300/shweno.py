@@ -93,7 +93,7 @@ def lib():
     L.shweno_fp64_probe.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, vp, dp, dp]
     L.shweno_flag_features.argtypes = [vp, vp]
     L.shweno_weight_deviation.argtypes = [vp, vp]
-    L.shweno_face_deviation.argtypes = [vp, vp]
+    L.shweno_face_deviation.argtypes = [vp, ctypes.c_double, vp]
     L.shweno_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
     L.shweno_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_float, vp, vp, vp]
     L.shweno_mlp_adam.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
@@ -238,9 +238,9 @@ def shweno_weight_deviation(h, out):
     _check(lib().shweno_weight_deviation(h, _ptr(out)[0]), h)
 
 
-def shweno_face_deviation(h, out):
+def shweno_face_deviation(h, out, floor_rel=1e-9):
     """out: CUDA float64 tensor [cells]."""
-    _check(lib().shweno_face_deviation(h, _ptr(out)[0]), h)
+    _check(lib().shweno_face_deviation(h, floor_rel, _ptr(out)[0]), h)
 
 
 def shweno_mlp_forward(params, x, prob, stream=0):

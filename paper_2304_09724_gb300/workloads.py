@@ -452,6 +452,33 @@ def constant_state(dim, eq, nx, ny=1, value=None):
     return st
 
 
+def smooth_flow_2d(seed, n, t_final=0.1, cfl=0.6, kmax=4):
+    """Seeded smooth periodic 2D Euler flow on (0,1)^2 (training data of the learned flag): for
+    each of rho, u, v, p a base value plus three random Fourier modes sin(2 pi k . x + phase),
+    k a nonzero integer vector with entries in -kmax..kmax.  The amplitude is 10^U[-10, -0.5]
+    times the base (rho, p) or 1 (u, v), so the data span nearly constant flows (a vortex's far
+    field) to strong smooth waves."""
+    rng = np.random.default_rng(60_000 + seed)
+    base = np.array([rng.uniform(0.5, 2.0), rng.uniform(-0.5, 0.5), rng.uniform(-0.5, 0.5), rng.uniform(0.5, 2.0)])
+    rel = 10.0 ** rng.uniform(-10.0, -0.5)
+    amp = np.array([base[0], 1.0, 1.0, base[3]]) * rel * rng.uniform(0.5, 1.0, size=4)
+    ks = []
+    while len(ks) < 3:
+        k = rng.integers(-kmax, kmax + 1, size=2)
+        if k.any():
+            ks.append(k)
+    a = rng.uniform(-1.0, 1.0, size=(4, 3)) / 3.0
+    ph = rng.uniform(0, 2 * math.pi, size=(4, 3))
+
+    def f(x, y):
+        fld = [base[c] + amp[c] * sum(a[c, m] * np.sin(2 * math.pi * (ks[m][0] * x + ks[m][1] * y) + ph[c, m])
+                                      for m in range(3)) for c in range(4)]
+        return euler_conserved(fld[0], fld[1], fld[3], fld[2])
+    W, V, Y, Z = project_2d(f, 0.0, 1.0, 0.0, 1.0, n, n)
+    return Workload(f"smooth2d_seed{seed}", 2, EULER, n, n, (0.0, 1.0, 0.0, 1.0), (PERIODIC,) * 4,
+                    t_final, cfl, {"W": W, "V": V, "Y": Y, "Z": Z})
+
+
 def random_smooth_1d(seed, nx, eq=EULER, amp=0.1):
     """Seeded smooth periodic data on (0,1): a few random Fourier modes on a positive state."""
     rng = np.random.default_rng(40_000 + seed)

@@ -35,7 +35,7 @@ def test_features_and_deviation_match_oracle():
     fd = torch.empty(40 * 40, dtype=torch.float64, device="cuda")
     S.shweno_flag_features(sol.h, x)
     S.shweno_weight_deviation(sol.h, d)
-    S.shweno_face_deviation(sol.h, fd)
+    S.shweno_face_deviation(sol.h, fd, 1e-9)
     t, _ = sol.time()
     sol.close()
     P = U.problem_of(wl)
@@ -54,6 +54,13 @@ def test_features_and_deviation_match_oracle():
     assert fo_.max() > 0.1
     tie = np.abs(fo_ - F.DELTA_FACE) < 1e-6
     assert np.array_equal((fg > F.DELTA_FACE)[~tie], (fo_ > F.DELTA_FACE)[~tie])
+    # a larger floor of the scale (changes measured against 1e-3 of the cell's own average too)
+    sol = U.solver_of(wl)
+    sol.set_state(st, t)
+    S.shweno_face_deviation(sol.h, fd, 1e-3)
+    sol.close()
+    np.testing.assert_allclose(fd.cpu().numpy(), O.face_deviation2d(P, st, t, floor_rel=1e-3).ravel(),
+                               rtol=1e-8, atol=1e-9)
 
 
 def test_network_kernels_match_oracle():
@@ -96,7 +103,7 @@ def test_training_from_scratch_on_the_gpu():
     Xv, yv = F.dataset([950, 951], n=96, times=(0.0, 0.05, 0.1))
     assert 0.0 < float(y.mean().item()) < 1.0
     hist = []
-    params, pw = F.train(X, y, epochs=10, batch=4096, seed=3, history=hist)
+    params, pw = F.train(X, y, epochs=30, batch=4096, seed=3, history=hist)
     start = F.mean_loss(torch.from_numpy(F.init_params(3)).cuda(), X, y, pw)
     end = F.mean_loss(params, X, y, pw)
     assert start / end >= 5.0, (start, end, hist)

@@ -99,6 +99,10 @@ def test_face_deviation_hand_case_and_limits():
     # a smooth quadratic barely moves the end values (the weights are close to linear and
     # p2, p3 differ from p1 by O(h^2)), a step moves them by a large fraction of the range
     assert O.face_deviation([0.0, 0.1, 0.3], [0.05, 0.25]) < 1e-3 * O.face_deviation([0.0, 0.0, 1.0], [0.0, 0.0])
+    # the floor of the scale: |p - p1| is the same, the scale grows by (floor - 1e-9) |W0|
+    Wb, v = [1.0, 1.0, 2.0], [0.0, 0.0]
+    d9, d3 = O.face_deviation(Wb, v), O.face_deviation(Wb, v, floor_rel=1e-3)
+    assert d3 == pytest.approx(d9 * (1.0 + 1e-9) / (1.0 + 1e-3), rel=1e-12)
 
 
 def test_face_deviation2d_cases():
