@@ -545,14 +545,15 @@ def bench_gpu(args):
 
 
 def bench_learned_run(args):
-    """Opt-in suite (--suite learned-run): the double Mach reflection (Example 5.10) run to its
-    final time T = 0.2 with the always-nonlinear weights, with the learned flag, and with the
+    """Opt-in suite (--suite learned-run): the double Mach reflection (Example 5.10) at --dmr-nx x
+    --dmr-nx/4 cells run with the always-nonlinear weights, with the learned flag, and with the
     always-nonlinear weights from initial averages perturbed by a relative 1e-12 (seeded signs),
-    at --dmr-nx x --dmr-nx/4 cells: wall time of each full run (CUDA events, device-side time
-    loop), steps, the learned form's flagged fraction at the end, and the relative L1 deviation of
-    the learned and of the perturbed solution from the plain one over all cell averages at T.  The
-    perturbed run measures how far two runs that differ at rounding level drift apart by T: the
-    floor below which no approximation of the weights can be told apart."""
+    each to the times --learned-t (default 0.2) in turn.  At every time: the relative L1 deviation
+    of the learned and of the perturbed solution from the plain one over all cell averages, the
+    learned form's flagged fraction, and each form's rate over the segment since the previous time
+    (CUDA events; device-side time loop).  The perturbed run measures how far two runs that differ
+    at rounding level drift apart: the floor below which no approximation of the weights can be
+    told apart."""
     import numpy as np
     import torch
 
@@ -562,11 +563,13 @@ def bench_learned_run(args):
 
     torch.cuda.set_device(0)
     nx = args.dmr_nx
+    times = [float(x) for x in args.learned_t.split(",")]
     wl = WL.dmr(nx, nx // 4)
     net = F.load()
-    out = {"suite": "learned-run", "workload": f"double Mach reflection {nx}x{nx // 4}, T = 0.2, CFL {CFL}",
-           "dtype": "f64", "data": "synthetic"}
-    states = {}
+    out = {"suite": "learned-run", "workload": f"double Mach reflection {nx}x{nx // 4}, CFL {CFL}",
+           "times": times, "dtype": "f64", "data": "synthetic"}
+    shape = (4, wl.ny, wl.nx)
+    snaps = {}
     for mode in ("plain", "learned", "perturbed"):
         stream = torch.cuda.Stream()
         sol = S.Solver(2, S.EULER, wl.nx, wl.ny, wl.domain, wl.bc, inflow=wl.inflow,
@@ -580,30 +583,42 @@ def bench_learned_run(args):
         if mode == "learned":
             S.shweno_set_flag_net(sol.h, torch.from_numpy(net[0]).cuda(), net[1])
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        status = "ok"
-        try:
-            t, n = sol.run(0.2, CFL)
-        except S.ShwenoError as e:
-            status = "nonphysical" if e.status == S.E_NONPHYSICAL else str(e)
-            t, n = sol.time()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        sec = e0.elapsed_time(e1) / 1000.0
-        res = {"status": status, "t": t, "steps": n, "seconds": sec,
-               "cell_updates_per_s": wl.nx * wl.ny * n / sec}
-        if mode == "learned":
-            fl = np.empty((wl.ny, wl.nx), dtype=np.uint8)
-            S.shweno_get_flags(sol.h, fl)
-            res["flagged_fraction_at_T"] = float(fl.mean())
-        states[mode] = sol.get_state()
+        rows, status, n_prev = [], "ok", 0
+        snaps[mode] = []
+        for T in times:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            try:
+                t, n = sol.run(T, CFL)
+            except S.ShwenoError as e:
+                status = "nonphysical" if e.status == S.E_NONPHYSICAL else str(e)
+                t, n = sol.time()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1000.0
+            row = {"T": T, "t": t, "steps": n, "seconds": sec,
+                   "cell_updates_per_s": wl.nx * wl.ny * (n - n_prev) / sec if sec > 0 else None}
+            n_prev = n
+            if mode == "learned":
+                fl = np.empty((wl.ny, wl.nx), dtype=np.uint8)
+                S.shweno_get_flags(sol.h, fl)
+                row["flagged_fraction"] = float(fl.mean())
+            Wd = torch.empty(shape, dtype=torch.float64, device="cuda")
+            dummy = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+            S.shweno_get_state(sol.h, Wd, *dummy)
+            snaps[mode].append(Wd)
+            del dummy
+            rows.append(row)
+            if status != "ok":
+                break
         sol.close()
-        out[mode] = res
-    a = states["plain"]["W"]
+        out[mode] = {"status": status, "rows": rows}
     for mode in ("learned", "perturbed"):
-        out[f"rel_l1_{mode}_vs_plain_W"] = float(np.sum(np.abs(states[mode]["W"] - a)) / np.sum(np.abs(a)))
-    out["speedup"] = out["learned"]["cell_updates_per_s"] / out["plain"]["cell_updates_per_s"]
+        for k, row in enumerate(out[mode]["rows"]):
+            a, b = snaps["plain"][k], snaps[mode][k]
+            row["rel_l1_vs_plain_W"] = float((b - a).abs().sum() / a.abs().sum())
+    for k, row in enumerate(out["learned"]["rows"]):
+        row["speedup_segment"] = row["cell_updates_per_s"] / out["plain"]["rows"][k]["cell_updates_per_s"]
     print(json.dumps(out), flush=True)
 
 
@@ -714,6 +729,7 @@ def main():
                                                       "refinement"])
     ap.add_argument("--n1d", type=int, default=4194304, help="euler1d: cells of the 1D problem")
     ap.add_argument("--dmr-nx", type=int, default=1024, help="learned-run: DMR mesh is N x N/4")
+    ap.add_argument("--learned-t", default="0.2", help="learned-run: comma-separated end times")
     ap.add_argument("--c5-problems", type=int, default=64)
     ap.add_argument("--refine-sizes", default="128,256,512,1024", help="refinement: mesh sides")
     ap.add_argument("--refine-t", type=float, default=1.0, help="refinement: final time")

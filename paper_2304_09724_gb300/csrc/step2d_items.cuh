@@ -22,8 +22,9 @@ constexpr int TX = 32;            // first-pass tile width
 // dv = v+ - v-, sv = v- + v+, p1's coefficient p at xi = +-1/2 is U_p + V_p and (-1)^p (U_p - V_p)
 // (U_p from the even monomials, V_p from the odd ones; end_u / end_v of recon_tables.cuh).
 struct EndTable {
-  double R[4][5][SEG];  // right end (xi = +1/2) of the cell in column c at slot c - 1: [comp][p][slot]
-  double L[4][5][SEG];  // left end (xi = -1/2)
+  // left ends (xi = -1/2) of the cells, two buffers (orders of even / odd K) so that one barrier
+  // per order suffices: [buffer][comp][p][slot], the cell in column c at slot c - 1
+  double L[2][4][5][SEG];
 };
 // Flags of the cells next to the faces, for the characteristic-wise path (whose weights belong to
 // each face point): lin[c] = 1 when the cell in column c uses the linear weights.
@@ -72,7 +73,7 @@ __device__ __forceinline__ void cell_mix(const Params& P, const double (*ev)[5][
 // A = 1, B = C = 0; the general form gives the same values bit for bit with more operations).
 template <int NC, bool LIN, bool Q, int K>
 __device__ __forceinline__ void cell_ends_t(const double (*ev)[5][SPAN], int c, const CellMix<NC>& m,
-                                            EndTable& et) {
+                                            EndTable& et, double eRo[NC][5]) {
   using namespace shweno_tables;
 #pragma unroll
   for (int q = 0; q < NC; ++q) {
@@ -111,17 +112,17 @@ __device__ __forceinline__ void cell_ends_t(const double (*ev)[5][SPAN], int c, 
           eL = (p & 1) ? fma(A, V, -AU) : fma(-A, V, AU);
         }
       }
-      et.R[q][p][c - 1] = eR;
-      et.L[q][p][c - 1] = eL;
+      eRo[q][p] = eR;
+      et.L[K & 1][q][p][c - 1] = eL;
     }
   }
 }
 // FLAGS = false: every cell is nonlinear (no branch on the flag); otherwise one branch per cell.
 template <int NC, bool FLAGS, bool Q, int K>
 __device__ __forceinline__ void cell_ends(const double (*ev)[5][SPAN], int c, const CellMix<NC>& m,
-                                          EndTable& et) {
-  if (FLAGS && m.lin) cell_ends_t<NC, true, Q, K>(ev, c, m, et);
-  else cell_ends_t<NC, false, Q, K>(ev, c, m, et);
+                                          EndTable& et, double eR[NC][5]) {
+  if (FLAGS && m.lin) cell_ends_t<NC, true, Q, K>(ev, c, m, et, eR);
+  else cell_ends_t<NC, false, Q, K>(ev, c, m, et, eR);
 }
 
 // Order K of the face point between cell columns f + 1 and f + 2: the two sides from the
@@ -129,20 +130,17 @@ __device__ __forceinline__ void cell_ends(const double (*ev)[5][SPAN], int c, co
 // eigen-decomposition of the upwinding; every derivative vector upwinded into a[q][m*5+n]
 // (m along x, n along y; dir = 0: x-face, p across = m; dir = 1: y-face, p across = n).
 template <int NC, int K>
-__device__ __forceinline__ void face_order(const Params& P, const EndTable& et, int f, int dir,
-                                           double Ws[NC], Upwinder<NC>& U, double a[NC][25]) {
-  double dl[NC][5], dr[NC][5];
+__device__ __forceinline__ void face_order(const Params& P, const EndTable& et, const double eR[NC][5], int f,
+                                           int dir, double Ws[NC], Upwinder<NC>& U, double a[NC][25]) {
+  double dr[NC][5];
 #pragma unroll
   for (int q = 0; q < NC; ++q)
 #pragma unroll
-    for (int p = 0; p + K <= 4; ++p) {
-      dl[q][p] = et.R[q][p][f];
-      dr[q][p] = et.L[q][p][f + 1];
-    }
+    for (int p = 0; p + K <= 4; ++p) dr[q][p] = et.L[K & 1][q][p][f + 1];
   if constexpr (K == 0) {
     double WL[NC], WR[NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) { WL[q] = dl[q][0]; WR[q] = dr[q][0]; }
+    for (int q = 0; q < NC; ++q) { WL[q] = eR[q][0]; WR[q] = dr[q][0]; }
     if constexpr (NC == 1) Ws[0] = burgers_godunov(WL[0], WR[0]);  // the same flux u^2/2 along x and y
     else hllc_state<NC>(WL, WR, P.gamma, dir, Ws);
     U.setup(Ws, P.gamma, dir, NC == 1 ? fmax(fabs(WL[0]), fabs(WR[0])) : 0.0);
@@ -152,7 +150,7 @@ __device__ __forceinline__ void face_order(const Params& P, const EndTable& et, 
     if (p == 0 && K == 0) continue;
     double x[NC], y[NC], o[NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) { x[q] = dl[q][p]; y[q] = dr[q][p]; }
+    for (int q = 0; q < NC; ++q) { x[q] = eR[q][p]; y[q] = dr[q][p]; }
     U.apply(x, y, o);
     const int idx = dir == 0 ? p * 5 + K : K * 5 + p;
 #pragma unroll
@@ -160,16 +158,18 @@ __device__ __forceinline__ void face_order(const Params& P, const EndTable& et, 
   }
 }
 
-// One order of the two-phase second pass: every cell thread writes its ends, then every face
-// thread upwinds them.  Called by all threads of the CTA (it holds the barriers).
+// One order of the two-phase second pass: every cell thread keeps its right ends and publishes its
+// left ends (buffer K & 1), one barrier, then every face thread upwinds its own cell's right end
+// against the next cell's left end.  The next order writes the other buffer, so a thread still
+// reading this one cannot be overtaken.  Called by all threads of the CTA (it holds the barrier).
 template <int NC, bool FLAGS, bool Q, int K>
 __device__ __forceinline__ void pass_order(const Params& P, const double (*ev)[5][SPAN], EndTable& et,
                                            bool has_cell, const CellMix<NC>& m, bool has_face,
                                            int dir, double Ws[NC], Upwinder<NC>& U, double a[NC][25]) {
-  if (has_cell) cell_ends<NC, FLAGS, Q, K>(ev, threadIdx.x + 1, m, et);
+  double eR[NC][5];
+  if (has_cell) cell_ends<NC, FLAGS, Q, K>(ev, threadIdx.x + 1, m, et, eR);
   __syncthreads();
-  if (has_face) face_order<NC, K>(P, et, threadIdx.x, dir, Ws, U, a);
-  __syncthreads();
+  if (has_face) face_order<NC, K>(P, et, eR, threadIdx.x, dir, Ws, U, a);
 }
 
 // Second pass, leading term, upwinding and CK of the nf faces of a CTA (nf <= NFACE): thread t
