@@ -403,6 +403,45 @@ def batched_2d(S, torch, WL, steps, problems):
     return res
 
 
+def bench_batched_full(args):
+    """Opt-in suite (--suite batched-full): the 512 seeded 1D Riemann problems of the batch run to
+    their end time T = 0.15 in one persistent launch (autotuned), every problem with its own CFL
+    step: wall time, cell-updates/s, steps per problem, the problems that leave the physical range.
+    (tests/test_gpu_batch_oracle.py holds problems of this set to the oracle at T = 0.15.)"""
+    import numpy as np
+    import torch
+
+    from paper_2304_09724_gb300 import shweno as S
+    from paper_2304_09724_gb300 import workloads as WL
+
+    torch.cuda.set_device(0)
+    make, updates, _, _ = _batch_tools(S, torch)
+    wls = [WL.random_riemann1d(s) for s in range(512)]
+    sols = make(wls)
+    b = S.Batch(sols)
+    tuned = b.autotune(0.15, CFL, trial_steps=2)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        st, per = b.run(0.15, CFL, check=False)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+    b.close()
+    steps = np.array([s.time()[1] for s in sols])
+    tend = np.array([s.time()[0] for s in sols])
+    n_upd = updates(sols, [0] * len(sols))
+    for s_ in sols:
+        s_.close()
+    ok = [x == S.OK for x in per]
+    print(json.dumps({"suite": "batched-full", "workload": "512 1D Euler Riemann problems to T = 0.15, N ~ U{400..16384}",
+                      "status": int(st), "seconds": el, "cell_updates": int(n_upd), "cell_updates_per_s": n_upd / el,
+                      "steps_per_problem": {"min": int(steps.min()), "mean": float(steps.mean()), "max": int(steps.max())},
+                      "reached_T": int(sum(1 for k in range(len(ok)) if ok[k] and tend[k] == 0.15)),
+                      "nonphysical_problems": int(sum(1 for x in per if x == S.E_NONPHYSICAL)),
+                      "autotuned": {"tile1d": tuned[0], "ctas_per_sm": tuned[1]}, "clocks": clk.summary(),
+                      "dtype": "f64", "data": "synthetic"}), flush=True)
+
+
 def bench_batched(args):
     """Opt-in suite (--suite batched): the two batched workloads with --steps steps per problem."""
     import torch
@@ -583,7 +622,7 @@ def bench_learned_run(args):
         if mode == "learned":
             S.shweno_set_flag_net(sol.h, torch.from_numpy(net[0]).cuda(), net[1])
         torch.cuda.synchronize()
-        rows, status, n_prev = [], "ok", 0
+        rows, status, n_total = [], "ok", 0
         snaps[mode] = []
         for T in times:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -596,9 +635,10 @@ def bench_learned_run(args):
             e1.record(stream)
             torch.cuda.synchronize()
             sec = e0.elapsed_time(e1) / 1000.0
-            row = {"T": T, "t": t, "steps": n, "seconds": sec,
-                   "cell_updates_per_s": wl.nx * wl.ny * (n - n_prev) / sec if sec > 0 else None}
-            n_prev = n
+            # run() returns the steps this call took: the segment since the previous time
+            n_total += n
+            row = {"T": T, "t": t, "steps": n, "steps_total": n_total, "seconds": sec,
+                   "cell_updates_per_s": wl.nx * wl.ny * n / sec if sec > 0 else None}
             if mode == "learned":
                 fl = np.empty((wl.ny, wl.nx), dtype=np.uint8)
                 S.shweno_get_flags(sol.h, fl)
@@ -725,8 +765,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="main line without the batched workloads")
     ap.add_argument("--c4-steps", type=int, default=10, help="steps per problem of the 1D batch on the main line")
     ap.add_argument("--c5-steps", type=int, default=2, help="steps per problem of the 2D batch on the main line")
-    ap.add_argument("--suite", default="main", choices=["main", "batched", "learned-run", "euler1d", "fp64-probe",
-                                                      "refinement"])
+    ap.add_argument("--suite", default="main", choices=["main", "batched", "batched-full", "learned-run", "euler1d",
+                                                      "fp64-probe", "refinement"])
     ap.add_argument("--n1d", type=int, default=4194304, help="euler1d: cells of the 1D problem")
     ap.add_argument("--dmr-nx", type=int, default=1024, help="learned-run: DMR mesh is N x N/4")
     ap.add_argument("--learned-t", default="0.2", help="learned-run: comma-separated end times")
@@ -746,6 +786,8 @@ def main():
         bench_learned_run(args)
     elif args.suite == "batched":
         bench_batched(args)
+    elif args.suite == "batched-full":
+        bench_batched_full(args)
     else:
         bench_gpu(args)
 
