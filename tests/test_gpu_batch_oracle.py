@@ -6,7 +6,9 @@ Example 5.1 runs to its end times in one persistent launch; every problem must t
 number of CFL steps, end at the oracle's time and hold the oracle's state (Section 2 and Section 3
 scheme, each problem with its own step size and end time; a problem that leaves the physical range
 must stop where the oracle stops).  A batch with the learned flag is advanced one step per launch,
-and the oracle is given the flags the batch used for that step and its own CFL step size."""
+and the oracle is given the flags the batch used for that step and its own CFL step size.  Four
+problems of the seeded 512-problem 1D set (their smallest meshes) run to the set's end time
+T = 0.15 in one launch and end where the oracle's full runs end."""
 import numpy as np
 import pytest
 
@@ -96,3 +98,25 @@ def test_learned_batch_step_by_step_equals_oracle_given_its_flags():
         s.close()
     # the flags are neither all on nor all off, so both kinds of cells were exercised
     assert 0.0 < min(flagged) and max(flagged) < 1.0
+
+
+def test_1d_riemann_set_to_its_end_time_equals_oracle():
+    small = sorted(range(512), key=lambda s: WL.random_riemann1d(s).nx)[:4]
+    wls = [WL.random_riemann1d(s) for s in small]
+    sols = []
+    for wl in wls:
+        s = U.solver_of(wl)
+        s.set_state(wl.state)
+        sols.append(s)
+    b = S.Batch(sols)
+    st, per = b.run(0.15, wls[0].cfl)
+    got = [(s.get_state(), s.time()) for s in sols]
+    b.close()
+    for s in sols:
+        s.close()
+    for wl, (g, (t, n)), status in zip(wls, got, per):
+        o, n_o, t_o, st_o = oracle_run(wl, 0.15)
+        what = f"{wl.name} {wl.nx} cells to T = 0.15"
+        assert status == st_o and n == n_o, (what, n, n_o)
+        assert t == pytest.approx(t_o, rel=1e-12), what
+        U.check(g, o, U.fields(wl), shocked=True, what=what, wl=wl)
