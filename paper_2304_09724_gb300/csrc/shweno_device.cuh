@@ -203,6 +203,31 @@ __device__ __forceinline__ void p1_coeffs(double Wm, double W0, double Wp, doubl
   c[4] = P1_C4_W0 * W0 + P1_C4_s * s + P1_C4_dv * dv;
 }
 
+// The three unnormalised weights of the cell (see shweno_mix) and their sum.
+struct RawWeights { double w1, w2, w3, sum; };
+__device__ __forceinline__ RawWeights shweno_raw_weights(const Params& P, double Wm, double W0, double Wp,
+                                                         const double c[5]) {
+  using namespace shweno_tables;
+  const double b1 = c[1] * (BETA_11 * c[1] + BETA_13 * c[3]) + BETA_33 * c[3] * c[3] +
+                    c[2] * (BETA_22 * c[2] + BETA_24 * c[4]) + BETA_44 * c[4] * c[4];
+  const double d2 = W0 - Wm, d3 = Wp - W0;
+  const double b2 = d2 * d2, b3 = d3 * d3;
+  double tau = 0.5 * (fabs(b1 - b2) + fabs(b1 - b3));
+  tau = tau * tau;
+  const double e1 = b1 + P.eps, e2 = b2 + P.eps, e3 = b3 + P.eps;
+  RawWeights r;
+  r.w1 = P.gam[0] * (e1 + tau) * (e2 * e3);
+  r.w2 = P.gam[1] * (e2 + tau) * (e1 * e3);
+  r.w3 = P.gam[2] * (e3 + tau) * (e1 * e2);
+  r.sum = r.w1 + r.w2 + r.w3;
+  return r;
+}
+// (A, B, C) from the unnormalised weights and inv = 1 / their sum.
+__device__ __forceinline__ Mix mix_from_raw(const Params& P, const RawWeights& r, double inv) {
+  const double A = r.w1 * inv * P.igam[0];
+  return Mix{A, r.w2 * inv - A * P.gam[1], r.w3 * inv - A * P.gam[2]};
+}
+
 __device__ __forceinline__ Mix shweno_mix(const Params& P, double Wm, double W0, double Wp,
                                           const double c[5], int nonlinear) {
   using namespace shweno_tables;
@@ -291,12 +316,14 @@ __device__ __forceinline__ void mix_coeffs_t(const Mix& m, double Wm, double W0,
 // ------------------------------------------------------------------ physics
 struct Prim {
   double rho, u, v, p, c, H;
+  double ir;  // 1 / rho
 };
 
 __device__ __forceinline__ Prim euler_prim(const double* W, int ncomp, double g) {
   Prim s;
   s.rho = W[0];
   const double ir = 1.0 / s.rho;
+  s.ir = ir;
   s.u = W[1] * ir;
   if (ncomp == 4) {
     s.v = W[2] * ir;
@@ -345,7 +372,7 @@ __device__ __forceinline__ void hllc_state(const double* WL, const double* WR, d
   const Prim& K = left ? L : R;
   const double S = left ? SL : SR, un = left ? uL : uR, mK = left ? mL : mR;
   const double f = mK / (S - Ss);
-  const double e = W[NC - 1] / K.rho + (Ss - un) * (Ss + K.p / mK);
+  const double e = W[NC - 1] * K.ir + (Ss - un) * (Ss + K.p / mK);
   out[0] = f;
   if (NC == 3) {
     out[1] = f * Ss;
@@ -355,6 +382,30 @@ __device__ __forceinline__ void hllc_state(const double* WL, const double* WR, d
     out[2 - dir] = f * (dir == 0 ? K.v : K.u);
     out[3] = f * e;
   }
+}
+
+// Physical flux along dir of a conserved state whose 1/rho is ir (Euler; unused for Burgers).
+template <int NC>
+__device__ __forceinline__ void phys_flux_ir(const double* W, double ir, double g, int dir, double* F) {
+  if (NC == 1) {
+    F[0] = 0.5 * W[0] * W[0];
+    return;
+  }
+  if (NC == 3) {
+    const double u = W[1] * ir;
+    const double p = (g - 1.0) * (W[2] - 0.5 * W[1] * u);
+    F[0] = W[1];
+    F[1] = W[1] * u + p;
+    F[2] = u * (W[2] + p);
+    return;
+  }
+  const double u = W[1] * ir, v = W[2] * ir;
+  const double p = (g - 1.0) * (W[3] - 0.5 * (W[1] * u + W[2] * v));
+  const double un = dir == 0 ? u : v;
+  F[0] = W[1 + dir];
+  F[1] = W[1] * un + (dir == 0 ? p : 0.0);
+  F[2] = W[2] * un + (dir == 1 ? p : 0.0);
+  F[3] = un * (W[3] + p);
 }
 
 // Physical flux along dir of a conserved state.

@@ -54,15 +54,36 @@ __device__ __forceinline__ void cell_mix(const Params& P, const double (*ev)[5][
     }
     return;
   }
+  if constexpr (NC == 4 && !Q) {
+    // the four components' weights normalised in pairs: 1/S0 = S1 / (S0 S1), 1/S1 = S0 / (S0 S1)
+    // (two divisions instead of four; the sums are products of smoothness indicators, far from
+    // the range where their product could overflow)
+    RawWeights rw[NC];
 #pragma unroll
-  for (int q = 0; q < NC; ++q) {
-    const double Wm = ev[q][0][c - 1], W0 = ev[q][0][c], Wp = ev[q][0][c + 1];
-    double cf[6];
-    p1_coeffs_t<Q>(Wm, W0, Wp, ev[NC + q][0][c - 1], ev[NC + q][0][c], ev[NC + q][0][c + 1], cf);
-    const Mix mm = shweno_mix_t<Q>(P, Wm, W0, Wp, cf, 1);
-    m.A[q] = mm.A;
-    m.B[q] = mm.B;
-    m.C[q] = mm.C;
+    for (int q = 0; q < NC; ++q) {
+      const double Wm = ev[q][0][c - 1], W0 = ev[q][0][c], Wp = ev[q][0][c + 1];
+      double cf[6];
+      p1_coeffs_t<Q>(Wm, W0, Wp, ev[NC + q][0][c - 1], ev[NC + q][0][c], ev[NC + q][0][c + 1], cf);
+      rw[q] = shweno_raw_weights(P, Wm, W0, Wp, cf);
+    }
+#pragma unroll
+    for (int h = 0; h < NC; h += 2) {
+      const double r = 1.0 / (rw[h].sum * rw[h + 1].sum);
+      const Mix m0 = mix_from_raw(P, rw[h], r * rw[h + 1].sum), m1 = mix_from_raw(P, rw[h + 1], r * rw[h].sum);
+      m.A[h] = m0.A; m.B[h] = m0.B; m.C[h] = m0.C;
+      m.A[h + 1] = m1.A; m.B[h + 1] = m1.B; m.C[h + 1] = m1.C;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const double Wm = ev[q][0][c - 1], W0 = ev[q][0][c], Wp = ev[q][0][c + 1];
+      double cf[6];
+      p1_coeffs_t<Q>(Wm, W0, Wp, ev[NC + q][0][c - 1], ev[NC + q][0][c], ev[NC + q][0][c + 1], cf);
+      const Mix mm = shweno_mix_t<Q>(P, Wm, W0, Wp, cf, 1);
+      m.A[q] = mm.A;
+      m.B[q] = mm.B;
+      m.C[q] = mm.C;
+    }
   }
 }
 
@@ -360,30 +381,45 @@ __device__ __forceinline__ void char_face_point(const Params& P, const double (*
   }
 }
 
-// Lobatto time average of the flux along dir and the state at tau = dt.
+// Lobatto time average of the flux along dir and the state at tau = dt.  Euler: the nodes tau > 0
+// share one division (1/rho1 = rho2 rho3 / (rho1 rho2 rho3) and so on).
 template <int NC>
 __device__ __forceinline__ void lobatto(const double tc[NC][5], double dt, double g, int dir,
                                         double Fh[NC], double We[NC]) {
   using namespace shweno_tables;
   const double taus[4] = {0.0, LOB_L1 * dt, LOB_L2 * dt, dt};
   const double wts[4] = {LOB_W0, LOB_W1, LOB_W1, LOB_W0};
+  double W[4][NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) W[0][q] = tc[q][0];  // tau = 0: the leading term itself
+#pragma unroll
+  for (int al = 1; al < 4; ++al)
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const double tau = taus[al];
+      W[al][q] = (((tc[q][4] * tau + tc[q][3]) * tau + tc[q][2]) * tau + tc[q][1]) * tau + tc[q][0];
+    }
+  double ir[4] = {0.0, 0.0, 0.0, 0.0};
+  if constexpr (NC > 1) {
+    ir[0] = 1.0 / W[0][0];
+    const double r23 = W[2][0] * W[3][0];
+    const double inv = 1.0 / (W[1][0] * r23);
+    ir[1] = inv * r23;
+    const double i23 = inv * W[1][0];  // 1 / (rho2 rho3)
+    ir[2] = i23 * W[3][0];
+    ir[3] = i23 * W[2][0];
+  }
 #pragma unroll
   for (int q = 0; q < NC; ++q) Fh[q] = 0.0;
 #pragma unroll
   for (int al = 0; al < 4; ++al) {
-    double W[NC], F[NC];
-    const double tau = taus[al];
-#pragma unroll
-    for (int q = 0; q < NC; ++q)
-      W[q] = (((tc[q][4] * tau + tc[q][3]) * tau + tc[q][2]) * tau + tc[q][1]) * tau + tc[q][0];
-    phys_flux<NC>(W, g, dir, F);
+    double F[NC];
+    phys_flux_ir<NC>(W[al], ir[al], g, dir, F);
 #pragma unroll
     for (int q = 0; q < NC; ++q) Fh[q] += wts[al] * F[q];
-    if (al == 3) {
-#pragma unroll
-      for (int q = 0; q < NC; ++q) We[q] = W[q];
-    }
   }
+#pragma unroll
+  for (int q = 0; q < NC; ++q) We[q] = W[3][q];
 }
 
 __device__ __forceinline__ double state_at(const double tc[5], double tau) {
