@@ -36,9 +36,9 @@ FP64_SLOTS_PER_S = 152 * 2 * 2.070e9  # FP64 thread instructions per second (DFM
 # pipe slot) per x-face point of xface2d, from ncu's instruction counters of the current kernel on
 # the 2048^2 launch, and its DRAM bytes per point from a capture at 512^2 (traffic grows in
 # proportion to the points).
-FLOPS_PER_XFACE_POINT = 5105.4
-FP64_INST_PER_XFACE_POINT = 3018.0
-DRAM_BYTES_PER_XFACE_POINT = 306.8
+FLOPS_PER_XFACE_POINT = 5028.1
+FP64_INST_PER_XFACE_POINT = 2984.5
+DRAM_BYTES_PER_XFACE_POINT = 308.0
 BYTES_PER_CELL_UPDATE = 256  # 16 doubles read + 16 written per cell (ideal reuse)
 
 
@@ -60,8 +60,10 @@ def method_flops_per_xface_launch(n):
       upwinding    eigenvectors at the leading term, 14 derivative vectors (difference, one
                    projection onto the acoustic wave that carries weight, its correction);
       ck           the generated Cauchy-Kovalevskaya recursion (its own term count);
-      flux         four Lobatto nodes: Horner in time, the physical flux, the weighted sum
-                   (a corner point only evaluates the state at the last node)."""
+      flux         four Lobatto nodes: Horner in time at the three nodes after the first (whose
+                   state is the leading term), the physical flux (one division for the three later
+                   nodes), the weighted sum (a corner point only evaluates the state at the last
+                   node)."""
     import importlib.util
 
     NC = 4
@@ -91,7 +93,7 @@ def method_flops_per_xface_launch(n):
     prim = 1 + 2 + 6 + 2 + 3
     leading = 2 * prim + 4 + 4 + 8 + 14
     upwind = prim + 40 + 14 * (NC + (2 * NC - 1) + 2 * NC)
-    flux = 4 * (NC * 2 * 4 + (1 + 14) + NC * 2)
+    flux = 3 * NC * 2 * 4 + 4 * 14 + (1 + 6) + 4 * NC * 2
     at_corner = NC * 2 * 4
     common = weights + end + leading + upwind + ck
     per_gauss = first_gauss + common + flux
