@@ -3,8 +3,9 @@
 The network and its training step run in the library's own CUDA kernels (shweno_mlp_forward,
 shweno_mlp_grad, shweno_mlp_adam through the C ABI); PyTorch only holds the device buffers.
 Labels come from the plain scheme itself: seeded random four-quadrant Riemann problems (rho ~
-U[0.1,2], u, v ~ U[-1,1], p ~ U[0.1,2]) at 256 x 256 and seeded smooth periodic flows of every
-amplitude from 1e-10 to 0.3 at 128^2 ... 2048^2 (workloads.smooth_flow_2d) are advanced with the
+U[0.1,2], u, v ~ U[-1,1], p ~ U[0.1,2]) at 256 x 256, seeded smooth periodic flows of every
+amplitude from 1e-10 to 0.3 at 128^2 ... 1024^2 (workloads.smooth_flow_2d) and seeded smooth
+Gaussian bumps at 256^2 ... 1024^2 (workloads.smooth_bumps_2d) are advanced with the
 always-nonlinear scheme; at several snapshots every cell gets the features of
 shweno_flag_features and the label 1 if shweno_face_deviation (floor FACE_FLOOR) exceeds
 DELTA_FACE: the nonlinear weights of some reconstruction anchored on the cell move its end values
@@ -48,13 +49,19 @@ def snapshot_data(seed, n=256, times=(0.0, 0.05, 0.1, 0.175, 0.25), label="face"
                   kind="quadrants", keep=1.0, kmax=4):
     """(features [k*cells][22], labels [k*cells], deviations) of one seeded problem (CUDA tensors):
     kind "quadrants" a four-quadrant Riemann problem, "smooth" a smooth periodic flow
-    (workloads.smooth_flow_2d); keep < 1 keeps that fraction of each snapshot's cells (seeded).
+    (workloads.smooth_flow_2d), "bumps" smooth Gaussian bumps (workloads.smooth_bumps_2d); keep < 1
+    keeps that fraction of each snapshot's cells (seeded).
     A problem whose plain run leaves the physical range keeps the snapshots taken before."""
     if delta is None:
         delta = DELTA_FACE if label == "face" else DELTA_WEIGHTS
     import torch
 
-    wl = WL.riemann2d(n, WL.random_quadrants(seed)) if kind == "quadrants" else WL.smooth_flow_2d(seed, n, kmax=kmax)
+    if kind == "quadrants":
+        wl = WL.riemann2d(n, WL.random_quadrants(seed))
+    elif kind == "smooth":
+        wl = WL.smooth_flow_2d(seed, n, kmax=kmax)
+    else:
+        wl = WL.smooth_bumps_2d(seed, n)
     sol = S.Solver(2, S.EULER, n, n, wl.domain, wl.bc, flag_mode=0)
     sol.set_state(wl.state)
     X, D = [], []
@@ -92,7 +99,8 @@ def dataset(seeds, **kw):
     return torch.cat([p[0] for p in parts]), torch.cat([p[1] for p in parts])
 
 
-SMOOTH_SIZES = (128, 256, 512, 1024, 2048)
+SMOOTH_SIZES = (128, 256, 512, 1024)
+BUMP_SIZES = (256, 512, 1024)
 
 
 def smooth_dataset(seeds, times=(0.0, 0.05), **kw):
@@ -106,6 +114,19 @@ def smooth_dataset(seeds, times=(0.0, 0.05), **kw):
         n = SMOOTH_SIZES[k % len(SMOOTH_SIZES)]
         parts.append(snapshot_data(s, n=n, times=times, kind="smooth", keep=min(1.0, 65536 / (n * n)),
                                    kmax=8 if k % 2 else 4, **kw))
+    return torch.cat([p[0] for p in parts]), torch.cat([p[1] for p in parts])
+
+
+def bump_dataset(seeds, times=(0.0, 0.05), **kw):
+    """Smooth localised structures (workloads.smooth_bumps_2d: Gaussian bumps of random width and
+    amplitude) at the mesh sizes BUMP_SIZES in turn, each snapshot thinned to about 65536 cells:
+    steep but resolved smooth features, which the quadrant problems only show next to jumps."""
+    import torch
+
+    parts = []
+    for k, s in enumerate(seeds):
+        n = BUMP_SIZES[k % len(BUMP_SIZES)]
+        parts.append(snapshot_data(s, n=n, times=times, kind="bumps", keep=min(1.0, 65536 / (n * n)), **kw))
     return torch.cat([p[0] for p in parts]), torch.cat([p[1] for p in parts])
 
 
@@ -193,28 +214,31 @@ def load(path=DEFAULT_WEIGHTS):
 
 def main():
     """The committed network's recipe: four-quadrant problems (seeds 100-111, 256^2, five
-    snapshots) and smooth flows (seeds 0-29) for training, seeds 500-503 and 1000-1009 for
-    validation, face-value labels, 15 epochs of Adam, the threshold that keeps recall 0.995 on the
-    validation data (the 3x3 dilation of the flags is the margin beyond it)."""
+    snapshots), smooth flows (seeds 0-29) and smooth bumps (seeds 0-23) for training, seeds
+    500-503, 1000-1009 and 1000-1007 for validation, face-value labels, 15 epochs of Adam, the
+    threshold that keeps recall 0.995 on the validation data (the 3x3 dilation of the flags is the
+    margin beyond it)."""
     import torch
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     ap.add_argument("--train-seeds", type=int, default=12)
     ap.add_argument("--smooth-seeds", type=int, default=30)
+    ap.add_argument("--bump-seeds", type=int, default=24)
     ap.add_argument("--val-seeds", type=int, default=4)
     ap.add_argument("--val-smooth-seeds", type=int, default=10)
+    ap.add_argument("--val-bump-seeds", type=int, default=8)
     ap.add_argument("--epochs", type=int, default=15)
     ap.add_argument("--recall", type=float, default=0.995)
     args = ap.parse_args()
     torch.cuda.set_device(0)
     t0 = time.time()
-    Xq, yq = dataset(range(100, 100 + args.train_seeds))
-    Xs, ys = smooth_dataset(range(0, args.smooth_seeds))
-    Xt, yt = torch.cat([Xq, Xs]), torch.cat([yq, ys])
-    Xvq, yvq = dataset(range(500, 500 + args.val_seeds))
-    Xvs, yvs = smooth_dataset(range(1000, 1000 + args.val_smooth_seeds))
-    Xv, yv = torch.cat([Xvq, Xvs]), torch.cat([yvq, yvs])
+    parts = [dataset(range(100, 100 + args.train_seeds)), smooth_dataset(range(0, args.smooth_seeds)),
+             bump_dataset(range(0, args.bump_seeds))]
+    Xt, yt = torch.cat([p[0] for p in parts]), torch.cat([p[1] for p in parts])
+    parts = [dataset(range(500, 500 + args.val_seeds)), smooth_dataset(range(1000, 1000 + args.val_smooth_seeds)),
+             bump_dataset(range(1000, 1000 + args.val_bump_seeds))]
+    Xv, yv = torch.cat([p[0] for p in parts]), torch.cat([p[1] for p in parts])
     t1 = time.time()
     params, pw = train(Xt, yt, epochs=args.epochs, log=print)
     torch.cuda.synchronize()

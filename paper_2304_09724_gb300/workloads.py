@@ -479,6 +479,31 @@ def smooth_flow_2d(seed, n, t_final=0.1, cfl=0.6, kmax=4):
                     t_final, cfl, {"W": W, "V": V, "Y": Y, "Z": Z})
 
 
+def smooth_bumps_2d(seed, n, t_final=0.1, cfl=0.6):
+    """Seeded smooth periodic 2D Euler flow on (0,1)^2 made of localised structures (training data
+    of the learned flag): a uniform state plus three Gaussian bumps exp(-r^2 / (2 w^2)) (periodic
+    distance r, width w ~ U[0.02, 0.15], random centre), each adding up to +-45 % of the base to
+    rho and p and up to +-1 to u and v."""
+    rng = np.random.default_rng(70_000 + seed)
+    base = np.array([rng.uniform(0.5, 2.0), rng.uniform(-0.5, 0.5), rng.uniform(-0.5, 0.5), rng.uniform(0.5, 2.0)])
+    cen = rng.uniform(0.0, 1.0, size=(3, 2))
+    wid = rng.uniform(0.02, 0.15, size=3)
+    amp = rng.uniform(-1.0, 1.0, size=(3, 4)) * np.array([0.15 * base[0], 0.33, 0.33, 0.15 * base[3]])
+
+    def f(x, y):
+        fld = [base[c] + 0.0 * (x + y) for c in range(4)]
+        for b in range(3):
+            dx = (x - cen[b, 0] + 0.5) % 1.0 - 0.5
+            dy = (y - cen[b, 1] + 0.5) % 1.0 - 0.5
+            g = np.exp(-(dx * dx + dy * dy) / (2.0 * wid[b] ** 2))
+            for c in range(4):
+                fld[c] = fld[c] + amp[b, c] * g
+        return euler_conserved(fld[0], fld[1], fld[3], fld[2])
+    W, V, Y, Z = project_2d(f, 0.0, 1.0, 0.0, 1.0, n, n)
+    return Workload(f"bumps2d_seed{seed}", 2, EULER, n, n, (0.0, 1.0, 0.0, 1.0), (PERIODIC,) * 4,
+                    t_final, cfl, {"W": W, "V": V, "Y": Y, "Z": Z})
+
+
 def random_smooth_1d(seed, nx, eq=EULER, amp=0.1):
     """Seeded smooth periodic data on (0,1): a few random Fourier modes on a positive state."""
     rng = np.random.default_rng(40_000 + seed)
