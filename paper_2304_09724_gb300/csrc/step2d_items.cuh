@@ -426,6 +426,32 @@ __device__ __forceinline__ double state_at(const double tc[5], double tau) {
   return (((tc[4] * tau + tc[3]) * tau + tc[2]) * tau + tc[1]) * tau + tc[0];
 }
 
+// Combined coefficients C[u] of NU = 1 or 2 components of one cell from their stencil averages
+// w[u] = (W-, W0, W+) and p1 coefficients c[u] (C = c for a cell with the linear weights).  PAIR
+// (Euler, reading R1): the two components' weights share one division, 1/S0 = S1 / (S0 S1) and
+// 1/S1 = S0 / (S0 S1), as in the second pass.
+template <bool Q, bool PAIR>
+__device__ __forceinline__ void first_pass_mix(const Params& P, int nl, const double (*w)[3], const double (*c)[6],
+                                               double (*C)[6]) {
+  constexpr int NU = PAIR ? 2 : 1;
+  if (!nl) {
+#pragma unroll
+    for (int u = 0; u < NU; ++u)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) C[u][k] = c[u][k];
+    return;
+  }
+  if constexpr (PAIR) {
+    const RawWeights r0 = shweno_raw_weights(P, w[0][0], w[0][1], w[0][2], c[0]);
+    const RawWeights r1 = shweno_raw_weights(P, w[1][0], w[1][1], w[1][2], c[1]);
+    const double inv = 1.0 / (r0.sum * r1.sum);
+    mix_coeffs_t<Q>(mix_from_raw(P, r0, inv * r1.sum), w[0][0], w[0][1], w[0][2], c[0], C[0]);
+    mix_coeffs_t<Q>(mix_from_raw(P, r1, inv * r0.sum), w[1][0], w[1][1], w[1][2], c[1], C[1]);
+  } else {
+    mix_coeffs_t<Q>(shweno_mix_t<Q>(P, w[0][0], w[0][1], w[0][2], c[0], 1), w[0][0], w[0][1], w[0][2], c[0], C[0]);
+  }
+}
+
 // First-pass polynomials of the cells of one tile: thread (tx, ty) of a TX x TYB block owns the
 // extended cell (bx + tx, by + ty); the 4 * NC fields of the tile plus a one-cell halo are staged
 // in shared memory `tile` (room for 16) by all nthreads threads first.  Q: reading R1', whose
@@ -453,24 +479,30 @@ __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv,
   const int lx = tx + 1, ly = ty + 1;
   const int NX4 = P.nx + 4, NY2 = P.ny + 2, NY4 = P.ny + 4;
   constexpr int KC = Q ? 6 : 5;
+  constexpr bool PAIR = NC == 4 && !Q;
+  constexpr int NU = PAIR ? 2 : 1;
   if (ic <= P.nx + 1 && jr >= -1 && jr <= P.ny) {  // y-pass: {W,Y} and {V,Z} along a column
     const int nl = cell_flag(P, flag, ic, jr);
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        const int fa = (s == 0 ? 0 : 1) * NC + q, fd = (s == 0 ? 2 : 3) * NC + q;
-        const double Wm = tile[fa][ly - 1][lx], W0 = tile[fa][ly][lx], Wp = tile[fa][ly + 1][lx];
-        const double vm = P.dy * tile[fd][ly - 1][lx], vp = P.dy * tile[fd][ly + 1][lx];
-        const double v0 = Q ? P.dy * tile[fd][ly][lx] : 0.0;
-        double c[6], C[6];
-        p1_coeffs_t<Q>(Wm, W0, Wp, vm, v0, vp, c);
-        if (nl) mix_coeffs_t<Q>(shweno_mix_t<Q>(P, Wm, W0, Wp, c, 1), Wm, W0, Wp, c, C);
-        else for (int k = 0; k < 6; ++k) C[k] = c[k];  // linear weights: p = p1
+      for (int q0 = 0; q0 < NC; q0 += NU) {
+        double w[NU][3], c[NU][6], C[NU][6];
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+          const int fa = (s == 0 ? 0 : 1) * NC + q0 + u, fd = (s == 0 ? 2 : 3) * NC + q0 + u;
+          w[u][0] = tile[fa][ly - 1][lx]; w[u][1] = tile[fa][ly][lx]; w[u][2] = tile[fa][ly + 1][lx];
+          const double vm = P.dy * tile[fd][ly - 1][lx], vp = P.dy * tile[fd][ly + 1][lx];
+          const double v0 = Q ? P.dy * tile[fd][ly][lx] : 0.0;
+          p1_coeffs_t<Q>(w[u][0], w[u][1], w[u][2], vm, v0, vp, c[u]);
+        }
+        first_pass_mix<Q, PAIR>(P, nl, w, c, C);
         const double sc = s == 0 ? 1.0 : P.dx;  // x-pass derivative data: dx * avg(W_x)
 #pragma unroll
-        for (int k = 0; k < KC; ++k)
-          ycoef[((size_t)((s * NC + q) * KC + k) * NY2 + (jr + 1)) * NX4 + (ic + 2)] = sc * C[k];
+        for (int u = 0; u < NU; ++u)
+#pragma unroll
+          for (int k = 0; k < KC; ++k)
+            ycoef[((size_t)((s * NC + q0 + u) * KC + k) * NY2 + (jr + 1)) * NX4 + (ic + 2)] = sc * C[u][k];
       }
   }
   if (ic >= 0 && ic < P.nx && jr <= P.ny + 1) {  // x-pass: {W,V} and {Y,Z} along a row
@@ -478,19 +510,23 @@ __device__ __forceinline__ void coef2d_item(const Params& P, const StepView& sv,
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        const int fa = (s == 0 ? 0 : 2) * NC + q, fd = (s == 0 ? 1 : 3) * NC + q;
-        const double Wm = tile[fa][ly][lx - 1], W0 = tile[fa][ly][lx], Wp = tile[fa][ly][lx + 1];
-        const double vm = P.dx * tile[fd][ly][lx - 1], vp = P.dx * tile[fd][ly][lx + 1];
-        const double v0 = Q ? P.dx * tile[fd][ly][lx] : 0.0;
-        double c[6], C[6];
-        p1_coeffs_t<Q>(Wm, W0, Wp, vm, v0, vp, c);
-        if (nl) mix_coeffs_t<Q>(shweno_mix_t<Q>(P, Wm, W0, Wp, c, 1), Wm, W0, Wp, c, C);
-        else for (int k = 0; k < 6; ++k) C[k] = c[k];  // linear weights: p = p1
+      for (int q0 = 0; q0 < NC; q0 += NU) {
+        double w[NU][3], c[NU][6], C[NU][6];
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+          const int fa = (s == 0 ? 0 : 2) * NC + q0 + u, fd = (s == 0 ? 1 : 3) * NC + q0 + u;
+          w[u][0] = tile[fa][ly][lx - 1]; w[u][1] = tile[fa][ly][lx]; w[u][2] = tile[fa][ly][lx + 1];
+          const double vm = P.dx * tile[fd][ly][lx - 1], vp = P.dx * tile[fd][ly][lx + 1];
+          const double v0 = Q ? P.dx * tile[fd][ly][lx] : 0.0;
+          p1_coeffs_t<Q>(w[u][0], w[u][1], w[u][2], vm, v0, vp, c[u]);
+        }
+        first_pass_mix<Q, PAIR>(P, nl, w, c, C);
         const double sc = s == 0 ? 1.0 : P.dy;  // y-pass derivative data: dy * avg(W_y)
 #pragma unroll
-        for (int k = 0; k < KC; ++k)
-          xcoef[((size_t)((s * NC + q) * KC + k) * P.nx + ic) * NY4 + (jr + 2)] = sc * C[k];
+        for (int u = 0; u < NU; ++u)
+#pragma unroll
+          for (int k = 0; k < KC; ++k)
+            xcoef[((size_t)((s * NC + q0 + u) * KC + k) * P.nx + ic) * NY4 + (jr + 2)] = sc * C[u][k];
       }
   }
 }
