@@ -312,8 +312,10 @@ def _batch_tools(S, torch):
     def updates(sols, before):
         return sum(s.nx * s.ny * (s.time()[1] - b) for s, b in zip(sols, before))
 
-    def timed_batch(sols, T, steps, tune):
+    def timed_batch(sols, T, steps, tune, mode=None):
         b = S.Batch(sols)
+        if mode is not None:
+            b.set_mode(mode)
         tuned = b.autotune(T, CFL, trial_steps=2) if tune else None
         before = [s.time()[1] for s in sols]
         torch.cuda.synchronize()
@@ -323,8 +325,9 @@ def _batch_tools(S, torch):
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
         n = updates(sols, before)
+        ran = "lockstep" if b.mode == S.BATCH_LOCKSTEP else "persistent"
         b.close()
-        return n / el, el, tuned, per, clk.summary()
+        return n / el, el, tuned, per, clk.summary(), ran
 
     def timed_solo(sols, steps):
         before = [s.time()[1] for s in sols]
@@ -350,7 +353,7 @@ def batched_1d(S, torch, WL, steps):
     make, _, timed_batch, timed_solo = _batch_tools(S, torch)
     wls = [WL.random_riemann1d(s) for s in range(512)]
     sols = make(wls)
-    rate_b, el_b, tuned, per, clk = timed_batch(sols, 0.15, steps, True)
+    rate_b, el_b, tuned, per, clk, _ = timed_batch(sols, 0.15, steps, True)
     for s in sols:
         s.close()
     sols = make(wls)
@@ -368,7 +371,9 @@ def batched_1d(S, torch, WL, steps):
 def batched_2d(S, torch, WL, steps, problems):
     """`problems` seeded four-quadrant 2D Riemann problems (rho ~ U[0.1,2], u, v ~ U[-1,1],
     p ~ U[0.1,2], sides 512..2048, end time 0.25): `steps` steps per problem, plain and learned
-    flag in one persistent launch each, against the plain handles advanced one after another."""
+    flag in the default mode (lockstep rounds for a batch of 2D problems) and plain in one
+    persistent launch, against the plain handles advanced one after another (each on its own
+    stream)."""
     import numpy as np
 
     from paper_2304_09724_gb300 import flagnet as F
@@ -378,9 +383,11 @@ def batched_2d(S, torch, WL, steps, problems):
     wls = [WL.random_riemann2d(s) for s in range(problems)]
     res = {"workload": f"{problems} 2D Euler four-quadrant Riemann problems, sides 512..2048, FP64, CFL 0.6",
            "problems": len(wls), "cells": int(sum(w.nx * w.ny for w in wls)), "steps_per_problem": steps}
-    for mode in ("plain", "learned"):
+    for mode in ("plain", "learned", "plain_persistent"):
         sols = make(wls, learned=(mode == "learned"), net=net)
-        r, el, _, per, clk = timed_batch(sols, 0.25, steps, False)
+        r, el, _, per, clk, ran = timed_batch(sols, 0.25, steps, False,
+                                              S.BATCH_PERSISTENT if mode == "plain_persistent" else None)
+        res[f"batch_{mode}_mode"] = ran
         res[f"batch_{mode}_cell_updates_per_s"] = r
         res[f"batch_{mode}_s"] = el
         res[f"batch_{mode}_clocks"] = clk
@@ -402,6 +409,7 @@ def batched_2d(S, torch, WL, steps, problems):
     res["per_instance_plain_s"] = el
     res["batch_plain_vs_per_instance"] = res["batch_plain_cell_updates_per_s"] / r
     res["batch_learned_vs_per_instance"] = res["batch_learned_cell_updates_per_s"] / r
+    res["batch_plain_persistent_vs_per_instance"] = res["batch_plain_persistent_cell_updates_per_s"] / r
     return res
 
 

@@ -229,16 +229,27 @@ shweno_status shweno_set_flag_net(shweno_handle* h, const float* params, double 
 /* Flags used by the last step (after dilation), [ny][nx] bytes. */
 shweno_status shweno_get_flags(shweno_handle* h, uint8_t* out, int on_device);
 
-/* ---------------------------------------------------------------- batched persistent launch
+/* ---------------------------------------------------------------- batched launches
  * Not in the paper: many independent problems (existing handles, 1D and 2D mixed, uneven sizes,
- * each with its own CFL time step and end time) advanced together by one persistent kernel,
- * launched from a CUDA graph.  Work items (problem, phase, index) flow through a device queue;
- * the CTA that finishes a problem's last item of a phase enqueues the next phase or commits the
- * step on the problem's own control block, so every handle stays usable on its own afterwards.
- * The only device-side wait is for an empty queue; it is bounded (about a second by default,
- * shweno_batch_set), after which the run returns SHWENO_E_TIMEOUT.  The handles must outlive
- * the batch and must not be used on their own while a batch run is in flight. */
+ * each with its own CFL time step and end time) advanced together.  Two modes:
+ *  - persistent: one persistent kernel, launched from a CUDA graph.  Work items (problem, phase,
+ *    index) flow through a device queue; the CTA that finishes a problem's last item of a phase
+ *    enqueues the next phase or commits the step.  The only device-side wait is for an empty
+ *    queue; it is bounded (about a second by default, shweno_batch_set), after which the run
+ *    returns SHWENO_E_TIMEOUT.
+ *  - lockstep: rounds of one launch per phase kind over the items of every running problem,
+ *    then a commit of every running problem's step (one round = one step of each); the host
+ *    reads the running count every 4 rounds.  No device-side wait.  Each CTA does one item, so
+ *    the 2D face items run at the one-mesh kernels' register budget without spilling.
+ * Both modes run the same items and the same step commit and give the same results bit for bit;
+ * each step is committed on the problem's own control block, so every handle stays usable on
+ * its own afterwards.  The handles must outlive the batch and must not be used on their own
+ * while a batch run is in flight. */
 typedef struct shweno_batch shweno_batch;
+
+/* Run modes (shweno_batch_set_mode).  AUTO: lockstep when every problem is 2D (their items are
+ * large enough that a launch per phase costs little), persistent otherwise. */
+enum { SHWENO_BATCH_AUTO = 0, SHWENO_BATCH_PERSISTENT = 1, SHWENO_BATCH_LOCKSTEP = 2 };
 
 /* Groups n handles.  cuda_stream: stream of the batch's work (NULL: its own).
  * Errors: INVALID (null or bad handle; a 2D handle created with charwise = 1 or any handle
@@ -255,10 +266,11 @@ shweno_status shweno_batch_create(shweno_handle* const* hs, int n, void* cuda_st
 shweno_status shweno_batch_run(shweno_batch* b, const double* t_final, double cfl, int64_t max_steps,
                                shweno_status* per_problem);
 
-/* Autotuner: times the candidate launch shapes (1D tile of 128..1024 cells; 1 or 2 CTAs per SM,
- * or 2..4 when every problem is 1D and the lighter 1D-only kernel runs) on trial_steps steps of
- * the actual problems, restoring every state afterwards, and keeps the fastest; the choice is
- * written to tile1d_out / ctas_per_sm_out (may be NULL). */
+/* Autotuner: times the candidate launch shapes of the persistent kernel (1D tile of 128..1024
+ * cells; 1 or 2 CTAs per SM, or 2..4 when every problem is 1D and the lighter 1D-only kernel
+ * runs) on trial_steps steps of the actual problems, restoring every state afterwards, and keeps
+ * the fastest; the choice is written to tile1d_out / ctas_per_sm_out (may be NULL).  The mode is
+ * left as it is (a lockstep run uses only the 1D tile). */
 shweno_status shweno_batch_autotune(shweno_batch* b, const double* t_final, double cfl,
                                     int64_t trial_steps, int* tile1d_out, int* ctas_per_sm_out);
 
@@ -266,6 +278,13 @@ shweno_status shweno_batch_autotune(shweno_batch* b, const double* t_final, doub
  * current setting).  tile1d: power of 2 in [128, 1024]; ctas_per_sm: 1 or 2 (1..4 for a batch
  * of 1D problems only).  Errors: INVALID (out of range). */
 shweno_status shweno_batch_set(shweno_batch* b, int tile1d, int ctas_per_sm, int64_t spin_limit);
+
+/* Sets the run mode (SHWENO_BATCH_AUTO, _PERSISTENT or _LOCKSTEP; the default is AUTO).
+ * Errors: INVALID (another value). */
+shweno_status shweno_batch_set_mode(shweno_batch* b, int mode);
+
+/* The mode the next run takes (SHWENO_BATCH_PERSISTENT or _LOCKSTEP; -1 for a null batch). */
+int shweno_batch_get_mode(const shweno_batch* b);
 
 shweno_status shweno_batch_destroy(shweno_batch* b);
 const char* shweno_batch_last_error(const shweno_batch* b);

@@ -100,11 +100,27 @@ __device__ bool begin_problem_step(const BatchProblem& B) {
   return true;
 }
 
+// End of a step for problem p (end_step of one mesh): a step that raised an error is not
+// committed (the state stays the last good one); otherwise t, the step count and the CFL rate
+// advance and the next step begins.  Returns false when the problem is done.
+__device__ bool commit_problem_step(const BatchProblem& B) {
+  volatile Ctl* c = B.ctl;
+  if (c->err != ERR_NONE) {
+    c->err_step = c->nsteps;
+    c->active = 0;
+    return false;
+  }
+  c->t = c->t + c->dt;
+  c->nsteps += 1;
+  c->rate_cur = c->rate_next;
+  return begin_problem_step(B);
+}
+
 // ------------------------------------------------------------------ the work of one item
 // HAS2D = false: a batch of 1D problems only; the 2D items are left out of the kernel, which
 // then needs about half the registers and runs more CTAs per SM.
 template <bool HAS2D>
-__device__ void do_item(const BatchProblem& B, int kind, long long idx, unsigned char* smem) {
+__device__ __forceinline__ void item_body(const BatchProblem& B, int kind, long long idx, unsigned char* smem) {
   const Params& P = B.P;
   Ctl* ctl = B.ctl;
   const StepView sv = step_view(ctl);
@@ -223,6 +239,13 @@ __device__ void do_item(const BatchProblem& B, int kind, long long idx, unsigned
   }
 }
 
+// The persistent kernel's call (left to the compiler's inlining choice: forcing it makes the
+// kernel spill far more).
+template <bool HAS2D>
+__device__ void do_item(const BatchProblem& B, int kind, long long idx, unsigned char* smem) {
+  item_body<HAS2D>(B, kind, idx, smem);
+}
+
 // ------------------------------------------------------------------ persistent kernel
 template <bool HAS2D>
 __global__ void __launch_bounds__(BT, HAS2D ? 1 : 4) batch_kernel(const BatchProblem* __restrict__ probs, int* pstate,
@@ -269,17 +292,7 @@ __global__ void __launch_bounds__(BT, HAS2D ? 1 : 4) batch_kernel(const BatchPro
         __threadfence();
         int next = ph + 1;
         if (next == B.nphase) {  // end of the step: commit (end_step) and start the next one
-          volatile Ctl* c = B.ctl;
-          bool go = false;
-          if (c->err != ERR_NONE) {
-            c->err_step = c->nsteps;
-            c->active = 0;
-          } else {
-            c->t = c->t + c->dt;
-            c->nsteps += 1;
-            c->rate_cur = c->rate_next;
-            go = begin_problem_step(B);
-          }
+          const bool go = commit_problem_step(B);
           next = 0;
           if (!go) {
             __threadfence();
@@ -349,6 +362,50 @@ __global__ void batch_config_kernel(const BatchProblem* __restrict__ probs, int 
   c->rate_cur = 0ull;
 }
 
+// ------------------------------------------------------------------ lockstep launches
+// The other way to run a batch: rounds of one launch per phase kind over the items of every
+// problem still running, then one thread per problem commits its step and begins the next (one
+// round = one step of every running problem).  Block b of the launch of kind k does item
+// b - start[p] of the problem p with start[p] <= b < start[p + 1] (start: prefix sums of the
+// problems' item counts of that kind).  Each CTA does one item and exits, so the face item
+// compiles as in the one-mesh kernels; in the persistent kernel's loop it does not fit in 255
+// registers and spills.  Items, step commit and step begin are the persistent kernel's, so the
+// two modes give the same results bit for bit.
+constexpr int kLockKinds[] = {PH_INFER, PH_DILATE, PH_COEF, PH_FACE, PH_UPDATE, PH_TILE1D};
+constexpr int kNumLockKinds = 6;
+
+template <int KIND>
+__global__ void __launch_bounds__(BT) lockstep_kernel(const BatchProblem* __restrict__ probs,
+                                                      const int* __restrict__ start, int n) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int lo = 0, hi = n;  // the last problem whose first block is at or before this one
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(start + mid) <= (int)blockIdx.x) lo = mid;
+    else hi = mid;
+  }
+  const BatchProblem& B = probs[lo];
+  if (!((const volatile Ctl*)B.ctl)->active) return;  // done, or stopped: its blocks idle
+  item_body<true>(B, KIND, (long long)blockIdx.x - __ldg(start + lo), smem);
+}
+
+// One thread per problem: commits the round's step of every running problem and counts the
+// problems that go on (bc->active, zeroed before the launch).
+__global__ void lockstep_commit_kernel(const BatchProblem* __restrict__ probs, int n, BatchCtl* bc) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const BatchProblem& B = probs[p];
+  if (!((const volatile Ctl*)B.ctl)->active) return;
+  if (commit_problem_step(B)) atomicAdd(&bc->active, 1);
+}
+
+// First step of every problem in lockstep mode (rates are already in rate_cur).
+__global__ void lockstep_seed_kernel(const BatchProblem* __restrict__ probs, int n, BatchCtl* bc) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  if (begin_problem_step(probs[p])) atomicAdd(&bc->active, 1);
+}
+
 }  // namespace shweno
 
 // ======================================================================== host side
@@ -379,6 +436,10 @@ struct shweno_batch {
   std::string err;
   cudaGraphExec_t graph = nullptr;
   std::vector<double> tuned;  // autotuner timings (ms) per candidate
+  int mode = SHWENO_BATCH_AUTO;  // SHWENO_BATCH_AUTO / _PERSISTENT / _LOCKSTEP
+  int* lstart = nullptr;         // lockstep block tables: [kind][problem + 1] prefix sums
+  std::vector<int> lstart_host;
+  int ltotal[shweno::kNumLockKinds] = {};
 };
 
 namespace {
@@ -497,7 +558,8 @@ shweno_status shweno_batch_create(shweno_handle* const* hs, int n, void* cuda_st
             cudaMalloc(&b->items, b->cap * sizeof(long long)) == cudaSuccess &&
             cudaMalloc(&b->seq, b->cap * sizeof(unsigned long long)) == cudaSuccess &&
             cudaMalloc(&b->chunk0, n * sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&b->t_final, n * sizeof(double)) == cudaSuccess;
+            cudaMalloc(&b->t_final, n * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&b->lstart, (size_t)kNumLockKinds * (n + 1) * sizeof(int)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     shweno_batch_destroy(b);
@@ -505,7 +567,9 @@ shweno_status shweno_batch_create(shweno_handle* const* hs, int n, void* cuda_st
   }
   if (cudaMemcpy(b->chunk0, ch.data(), n * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaFuncSetAttribute(batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem) != cudaSuccess ||
-      cudaFuncSetAttribute(batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem1D) != cudaSuccess) {
+      cudaFuncSetAttribute(batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem1D) != cudaSuccess ||
+      cudaFuncSetAttribute(lockstep_kernel<PH_FACE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFaceSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(lockstep_kernel<PH_TILE1D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem1D) != cudaSuccess) {
     cudaGetLastError();
     shweno_batch_destroy(b);
     return SHWENO_E_CUDA;
@@ -525,6 +589,7 @@ shweno_status shweno_batch_destroy(shweno_batch* b) {
   cudaFree(b->seq);
   cudaFree(b->chunk0);
   cudaFree(b->t_final);
+  cudaFree(b->lstart);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return SHWENO_OK;
@@ -554,7 +619,8 @@ void enqueue_batch(shweno_batch* b, double cfl) {
                                                                   cap - 1, b->spin_limit);
 }
 
-shweno_status run_once(shweno_batch* b, const double* t_final, double cfl, int64_t max_steps, bool graph) {
+// Problem table, start step counts and end times of one run, uploaded on b->stream.
+shweno_status prepare_run(shweno_batch* b, const double* t_final, int64_t max_steps) {
   using namespace shweno;
   const int n = (int)b->views.size();
   for (int p = 0; p < n; ++p) {
@@ -571,6 +637,14 @@ shweno_status run_once(shweno_batch* b, const double* t_final, double cfl, int64
   if (cudaMemcpyAsync(b->probs, b->host_probs.data(), n * sizeof(BatchProblem), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
       cudaMemcpyAsync(b->t_final, t_final, n * sizeof(double), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
     return bfail(b, SHWENO_E_CUDA, "upload failed");
+  return SHWENO_OK;
+}
+
+// One persistent-kernel run (from the cached graph when `graph`).
+shweno_status run_once(shweno_batch* b, const double* t_final, double cfl, int64_t max_steps, bool graph) {
+  using namespace shweno;
+  const shweno_status ps = prepare_run(b, t_final, max_steps);
+  if (ps != SHWENO_OK) return ps;
   if (graph) {
     if (!b->graph) {
       cudaGraph_t g = nullptr;
@@ -595,6 +669,94 @@ shweno_status run_once(shweno_batch* b, const double* t_final, double cfl, int64
   return SHWENO_OK;
 }
 
+// Dynamic shared memory of a lockstep launch of one kind.
+size_t lock_smem(const shweno_batch* b, int kind) {
+  using namespace shweno;
+  switch (kind) {
+    case PH_INFER: return sizeof(float) * NPARAM;
+    case PH_COEF: return sizeof(double) * 16 * (TYB + 2) * (TX + 2);
+    case PH_FACE: return kFaceSmem;
+    case PH_TILE1D: return sizeof(double) * 2 * 3 * (b->tile1d + 1);
+    default: return 0;
+  }
+}
+
+void launch_lock(shweno_batch* b, int kind, const int* start, int grid) {
+  using namespace shweno;
+  const int n = (int)b->views.size();
+  const size_t sm = lock_smem(b, kind);
+  switch (kind) {
+    case PH_INFER: lockstep_kernel<PH_INFER><<<grid, BT, sm, b->stream>>>(b->probs, start, n); break;
+    case PH_DILATE: lockstep_kernel<PH_DILATE><<<grid, BT, sm, b->stream>>>(b->probs, start, n); break;
+    case PH_COEF: lockstep_kernel<PH_COEF><<<grid, BT, sm, b->stream>>>(b->probs, start, n); break;
+    case PH_FACE: lockstep_kernel<PH_FACE><<<grid, BT, sm, b->stream>>>(b->probs, start, n); break;
+    case PH_UPDATE: lockstep_kernel<PH_UPDATE><<<grid, BT, sm, b->stream>>>(b->probs, start, n); break;
+    default: lockstep_kernel<PH_TILE1D><<<grid, BT, sm, b->stream>>>(b->probs, start, n); break;
+  }
+}
+
+// One lockstep run: rates and first steps, then rounds of (one launch per phase kind with work,
+// the commit) until no problem runs, reading the running count back every few rounds.
+shweno_status run_lockstep(shweno_batch* b, const double* t_final, double cfl, int64_t max_steps) {
+  using namespace shweno;
+  const shweno_status ps = prepare_run(b, t_final, max_steps);
+  if (ps != SHWENO_OK) return ps;
+  const int n = (int)b->views.size();
+  // block tables: start[k][p] = first block of problem p in the launch of kind k
+  b->lstart_host.assign((size_t)kNumLockKinds * (n + 1), 0);
+  for (int k = 0; k < kNumLockKinds; ++k) {
+    long long acc = 0;
+    for (int p = 0; p < n; ++p) {
+      b->lstart_host[(size_t)k * (n + 1) + p] = (int)acc;
+      const BatchProblem& B = b->host_probs[p];
+      for (int f = 0; f < B.nphase; ++f)
+        if (B.phase_kind[f] == kLockKinds[k]) acc += B.nitems[f];
+      if (acc > INT32_MAX) return bfail(b, SHWENO_E_INVALID, "too many items for one lockstep launch");
+    }
+    b->lstart_host[(size_t)k * (n + 1) + n] = (int)acc;
+    b->ltotal[k] = (int)acc;
+  }
+  if (cudaMemcpyAsync(b->lstart, b->lstart_host.data(), b->lstart_host.size() * sizeof(int), cudaMemcpyHostToDevice,
+                      b->stream) != cudaSuccess)
+    return bfail(b, SHWENO_E_CUDA, "upload failed");
+  int* active = &b->bc->active;
+  batch_config_kernel<<<(n + 127) / 128, 128, 0, b->stream>>>(b->probs, n, b->t_final, cfl);
+  batch_rate_kernel<<<b->nchunks, 256, 0, b->stream>>>(b->probs, b->chunk0, n);
+  cudaMemsetAsync(b->bc, 0, sizeof(BatchCtl), b->stream);
+  lockstep_seed_kernel<<<(n + 127) / 128, 128, 0, b->stream>>>(b->probs, n, b->bc);
+  const int kChunk = 4;  // rounds between two reads of the running count
+  int64_t rounds = 0;
+  for (;;) {
+    int running = 0;
+    if (cudaMemcpyAsync(&running, active, sizeof(int), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+      return bfail(b, SHWENO_E_CUDA, "reading the running count failed");
+    const cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, SHWENO_E_CUDA, std::string("lockstep round: ") + cudaGetErrorString(e));
+    if (running == 0 || (max_steps > 0 && rounds >= max_steps)) break;
+    int64_t r = kChunk;
+    if (max_steps > 0) r = std::min<int64_t>(r, max_steps - rounds);
+    for (int64_t i = 0; i < r; ++i) {
+      for (int k = 0; k < kNumLockKinds; ++k)
+        if (b->ltotal[k] > 0) launch_lock(b, kLockKinds[k], b->lstart + (size_t)k * (n + 1), b->ltotal[k]);
+      cudaMemsetAsync(active, 0, sizeof(int), b->stream);
+      lockstep_commit_kernel<<<(n + 127) / 128, 128, 0, b->stream>>>(b->probs, n, b->bc);
+    }
+    const cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) return bfail(b, SHWENO_E_CUDA, std::string("lockstep launch: ") + cudaGetErrorString(le));
+    rounds += r;
+  }
+  return SHWENO_OK;
+}
+
+// The mode a run takes: lockstep when set, or in auto mode when every problem is 2D.
+bool use_lockstep(const shweno_batch* b) {
+  if (b->mode == SHWENO_BATCH_LOCKSTEP) return true;
+  if (b->mode == SHWENO_BATCH_PERSISTENT) return false;
+  for (const auto& v : b->views)
+    if (v.P.dim != 2) return false;
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -608,7 +770,8 @@ shweno_status shweno_batch_run(shweno_batch* b, const double* t_final, double cf
   static thread_local double last_cfl = -1.0;
   if (b->graph && cfl != last_cfl) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
   last_cfl = cfl;
-  shweno_status s = run_once(b, t_final, cfl, max_steps, max_steps <= 0);
+  shweno_status s = use_lockstep(b) ? run_lockstep(b, t_final, cfl, max_steps)
+                                    : run_once(b, t_final, cfl, max_steps, max_steps <= 0);
   if (per_problem) {
     for (int p = 0; p < n; ++p) {
       Ctl c;
@@ -718,6 +881,19 @@ shweno_status shweno_batch_set(shweno_batch* b, int tile1d, int ctas_per_sm, int
   if (spin_limit > 0) b->spin_limit = spin_limit;
   if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
   return SHWENO_OK;
+}
+
+shweno_status shweno_batch_set_mode(shweno_batch* b, int mode) {
+  if (!b) return SHWENO_E_INVALID;
+  if (mode != SHWENO_BATCH_AUTO && mode != SHWENO_BATCH_PERSISTENT && mode != SHWENO_BATCH_LOCKSTEP)
+    return bfail(b, SHWENO_E_INVALID, "mode must be SHWENO_BATCH_AUTO, _PERSISTENT or _LOCKSTEP");
+  b->mode = mode;
+  return SHWENO_OK;
+}
+
+int shweno_batch_get_mode(const shweno_batch* b) {
+  if (!b) return -1;
+  return use_lockstep(b) ? SHWENO_BATCH_LOCKSTEP : SHWENO_BATCH_PERSISTENT;
 }
 
 }  // extern "C"

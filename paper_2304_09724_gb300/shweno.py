@@ -52,8 +52,9 @@ EXPORTS = ["shweno_create", "shweno_set_state", "shweno_get_state", "shweno_step
            "shweno_mlp_grad",
            "shweno_mlp_adam", "shweno_set_flag_net", "shweno_get_flags", "shweno_batch_create",
            "shweno_batch_run", "shweno_batch_autotune", "shweno_batch_set", "shweno_batch_destroy",
-           "shweno_batch_last_error"]
+           "shweno_batch_last_error", "shweno_batch_set_mode", "shweno_batch_get_mode"]
 FLAG_FEATURES, FLAG_PARAMS = 22, 1825
+BATCH_AUTO, BATCH_PERSISTENT, BATCH_LOCKSTEP = 0, 1, 2
 NOALLOC_MAX_NX = 65536
 
 _lib = None
@@ -108,10 +109,14 @@ def lib():
     L.shweno_batch_destroy.argtypes = [vp]
     L.shweno_batch_last_error.argtypes = [vp]
     L.shweno_batch_last_error.restype = ctypes.c_char_p
+    L.shweno_batch_set_mode.argtypes = [vp, ctypes.c_int]
+    L.shweno_batch_get_mode.argtypes = [vp]
+    L.shweno_batch_get_mode.restype = ctypes.c_int
     L.shweno_last_error.argtypes = [vp]
     L.shweno_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("shweno_last_error", "shweno_kernel_name", "shweno_batch_last_error"):
+        if name not in ("shweno_last_error", "shweno_kernel_name", "shweno_batch_last_error",
+                        "shweno_batch_get_mode"):
             getattr(L, name).restype = st
     _lib = L
     return L
@@ -277,7 +282,8 @@ def shweno_last_error(h=None):
 
 
 class Batch:
-    """Many handles advanced by one persistent launch (shweno_batch_*)."""
+    """Many handles advanced together (shweno_batch_*): one persistent launch, or lockstep rounds
+    of one launch per phase (the default for batches of 2D problems)."""
 
     def __init__(self, solvers, stream=0):
         self.solvers = list(solvers)  # keeps the handles alive
@@ -310,6 +316,15 @@ class Batch:
 
     def set(self, tile1d=0, ctas_per_sm=0, spin_limit=0):
         self._err(lib().shweno_batch_set(self.b, tile1d, ctas_per_sm, spin_limit))
+
+    def set_mode(self, mode):
+        """BATCH_AUTO, BATCH_PERSISTENT or BATCH_LOCKSTEP (shweno_batch_set_mode)."""
+        self._err(lib().shweno_batch_set_mode(self.b, mode))
+
+    @property
+    def mode(self):
+        """The mode the next run takes: BATCH_PERSISTENT or BATCH_LOCKSTEP."""
+        return lib().shweno_batch_get_mode(self.b)
 
     def close(self):
         if self.b:

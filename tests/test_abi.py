@@ -20,7 +20,7 @@ def declared_functions():
         if h.endswith(".h"):
             src = open(os.path.join(ROOT, "include", h)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names += re.findall(r"^\s*(?:shweno_status|const char\*)\s+(shweno_\w+)\s*\(", src, flags=re.M)
+            names += re.findall(r"^\s*(?:shweno_status|const char\*|int)\s+(shweno_\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 

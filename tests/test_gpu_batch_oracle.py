@@ -6,7 +6,8 @@ Example 5.1 runs to its end times in one persistent launch; every problem must t
 number of CFL steps, end at the oracle's time and hold the oracle's state (Section 2 and Section 3
 scheme, each problem with its own step size and end time; a problem that leaves the physical range
 must stop where the oracle stops).  A batch with the learned flag is advanced one step per launch,
-and the oracle is given the flags the batch used for that step and its own CFL step size.  Four
+and the oracle is given the flags the batch used for that step and its own CFL step size (in
+both modes: the persistent kernel and lockstep rounds).  Four
 problems of the seeded 512-problem 1D set (their smallest meshes) run to the set's end time
 T = 0.15 in one launch and end where the oracle's full runs end."""
 import numpy as np
@@ -58,7 +59,8 @@ def test_mixed_ragged_batch_equals_oracle():
         U.check(g, o, U.fields(wl), shocked=True, what=what, wl=wl)
 
 
-def test_learned_batch_step_by_step_equals_oracle_given_its_flags():
+@pytest.mark.parametrize("mode", [S.BATCH_PERSISTENT, S.BATCH_LOCKSTEP])
+def test_learned_batch_step_by_step_equals_oracle_given_its_flags(mode):
     import torch
 
     torch.cuda.set_device(0)
@@ -74,6 +76,7 @@ def test_learned_batch_step_by_step_equals_oracle_given_its_flags():
             S.shweno_set_flag_net(s.h, *net)
         sols.append(s)
     b = S.Batch(sols)
+    b.set_mode(mode)
     orc = [{"P": U.problem_of(wl), "state": wl.state, "t": 0.0} for wl in wls]
     flagged = []
     for k in range(4):
