@@ -75,6 +75,14 @@ def test_invalid_arguments_rejected_before_device_use(built):
     # null handle
     assert L.shweno_step(None, 0.1) == S.E_INVALID
     assert L.shweno_destroy(None) == S.OK
+    # batch entry points: a null batch or an empty handle list is refused before any device use
+    b = ctypes.c_void_p()
+    assert L.shweno_batch_create(None, 1, None, ctypes.byref(b)) == S.E_INVALID
+    assert L.shweno_batch_create((ctypes.c_void_p * 1)(None), 0, None, ctypes.byref(b)) == S.E_INVALID
+    assert L.shweno_batch_set_mode(None, S.BATCH_LOCKSTEP) == S.E_INVALID
+    assert L.shweno_batch_get_mode(None) == -1
+    assert L.shweno_batch_set(None, 256, 1, 0) == S.E_INVALID
+    assert L.shweno_batch_destroy(None) == S.OK
 
 
 def test_binding_raises_without_library(monkeypatch, tmp_path):
