@@ -241,9 +241,10 @@ shweno_status shweno_get_flags(shweno_handle* h, uint8_t* out, int on_device);
  *    then a commit of every running problem's step (one round = one step of each); the host
  *    reads the running count every 4 rounds.  No device-side wait.  Each CTA does one item, so
  *    the 2D face items run at the one-mesh kernels' register budget without spilling.
- * Both modes run the same items and the same step commit and give the same results bit for bit;
- * each step is committed on the problem's own control block, so every handle stays usable on
- * its own afterwards.  The handles must outlive the batch and must not be used on their own
+ * Both modes run the same items and the same step commit: the same step counts and times, states
+ * equal to round-off (the compiler may fuse a product into a multiply-add differently in the two
+ * kernels).  Each step is committed on the problem's own control block, so every handle stays
+ * usable on its own afterwards.  The handles must outlive the batch and must not be used on their own
  * while a batch run is in flight. */
 typedef struct shweno_batch shweno_batch;
 

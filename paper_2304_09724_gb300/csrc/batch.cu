@@ -370,7 +370,8 @@ __global__ void batch_config_kernel(const BatchProblem* __restrict__ probs, int 
 // problems' item counts of that kind).  Each CTA does one item and exits, so the face item
 // compiles as in the one-mesh kernels; in the persistent kernel's loop it does not fit in 255
 // registers and spills.  Items, step commit and step begin are the persistent kernel's, so the
-// two modes give the same results bit for bit.
+// two modes take the same steps; their states agree to round-off (the same functions inlined
+// into different kernels may contract a product into a fused multiply-add differently).
 constexpr int kLockKinds[] = {PH_INFER, PH_DILATE, PH_COEF, PH_FACE, PH_UPDATE, PH_TILE1D};
 constexpr int kNumLockKinds = 6;
 
