@@ -271,7 +271,8 @@ shweno_status shweno_batch_run(shweno_batch* b, const double* t_final, double cf
  * cells; 1 or 2 CTAs per SM, or 2..4 when every problem is 1D and the lighter 1D-only kernel
  * runs) on trial_steps steps of the actual problems, restoring every state afterwards, and keeps
  * the fastest; the choice is written to tile1d_out / ctas_per_sm_out (may be NULL).  The mode is
- * left as it is (a lockstep run uses only the 1D tile). */
+ * left as it is (a lockstep run uses only the 1D tile); a batch of 2D problems in lockstep mode
+ * has nothing to tune, and the call returns the current settings without running anything. */
 shweno_status shweno_batch_autotune(shweno_batch* b, const double* t_final, double cfl,
                                     int64_t trial_steps, int* tile1d_out, int* ctas_per_sm_out);
 

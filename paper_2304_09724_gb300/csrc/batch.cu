@@ -796,6 +796,12 @@ shweno_status shweno_batch_autotune(shweno_batch* b, const double* t_final, doub
   const int n = (int)b->views.size();
   bool any1d = false;
   for (auto& v : b->views) any1d |= v.P.dim == 1;
+  if (!any1d && use_lockstep(b)) {  // lockstep rounds of 2D problems have no launch shape to tune
+    b->tuned.clear();
+    if (tile1d_out) *tile1d_out = b->tile1d;
+    if (ctas_per_sm_out) *ctas_per_sm_out = b->ctas_per_sm;
+    return SHWENO_OK;
+  }
   // backups of the states and control blocks
   std::vector<double*> bk(n, nullptr);
   std::vector<Ctl> cbk(n);

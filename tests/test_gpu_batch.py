@@ -189,7 +189,8 @@ def test_lockstep_and_persistent_modes_agree():
     """The same mixed batch (1D and 2D Euler, 2D Burgers, learned-flag 2D problems, one problem
     that turns non-physical, uneven end times) in both modes: the same statuses, step counts and
     times, states equal to round-off; the default mode is lockstep for a batch of 2D problems only
-    and persistent otherwise; an unknown mode is refused."""
+    and persistent otherwise; the autotuner has nothing to tune for a lockstep batch of 2D
+    problems; an unknown mode is refused."""
     import torch
 
     from paper_2304_09724_gb300 import flagnet as F
@@ -232,6 +233,9 @@ def test_lockstep_and_persistent_modes_agree():
         s.set_state(wl.state)
     b = S.Batch(only2d)
     assert b.mode == S.BATCH_LOCKSTEP
+    # nothing to tune in lockstep rounds of 2D problems: the current shape comes back, nothing runs
+    assert b.autotune(0.01, wls[0].cfl) == (512, 2)
+    assert all(s.time() == (0.0, 0) for s in only2d)
     b.set_mode(S.BATCH_PERSISTENT)
     assert b.mode == S.BATCH_PERSISTENT
     with pytest.raises(S.ShwenoError) as e:
